@@ -1,0 +1,47 @@
+"""Write the stored expected growth vectors of the large workloads.
+
+Every value written here comes from the CPU oracle (``oracle/``) and nothing else.  Run from
+the repository root:  python tests/golden/make_golden.py [name ...]
+"""
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import workloads as w  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+CASES = {
+    # name: (n, gens, two_layer, max_radius, description)
+    "s11_lrx_growth": (11, w.lrx(11), True, -1,
+                       "S_11, LRX generators, full growth from the identity"),
+    "s14_pancake_layers": (14, w.pancake(14), True, 8,
+                           "S_14, 13 prefix reversals, layers 0..8 from the identity"),
+    "s10_lx_growth": (10, w.lx(10), False, -1,
+                                   "S_10, LX generators (directed), full growth"),
+}
+
+
+def write(name):
+    n, gens, two, maxr, desc = CASES[name]
+    t0 = time.time()
+    g, rc = oracle.growth(n, gens, two_layer=two, max_radius=maxr)
+    dt = time.time() - t0
+    path = os.path.join(HERE, name + ".txt")
+    with open(path, "w") as f:
+        f.write(f"# {desc}\n")
+        f.write(f"# written by tests/golden/make_golden.py from the CPU oracle "
+                f"({'two-layer' if two else 'full visited'} mode, max_radius={maxr}, "
+                f"{dt:.0f} s)\n")
+        for r, c in enumerate(g):
+            f.write(f"{r} {c}\n")
+    print(name, len(g), sum(g), f"{dt:.1f}s")
+
+
+if __name__ == "__main__":
+    for name in (sys.argv[1:] or list(CASES)):
+        write(name)
