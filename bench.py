@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 growth library: neighbour states generated + deduplicated per second.
+
+One step = one complete growth of the workload through the library's C ABI (default: S_11 with
+the LRX generators, 39,916,800 states, 56 layers, every layer expanded).  `value` is timed on the
+device (CUDA events on the run's stream, inputs resident: the handle and its buffers exist before
+the timed region); `e2e` is the same metric through the public Python call `growth()` with host
+inputs and outputs, host<->device copies inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload s11_lrx|s8_coxeter|s14_pancake|batch]
+    python bench.py --impl reference ...     # the CPU oracle on a bounded sample, same metric
+
+Multi-GPU (torchrun): every rank grows its own replica of the workload (the growth of one graph
+has no partition without an exchange step; the library runs one GPU), value = all ranks' work /
+max-over-ranks time, scaling "weak".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "neighbour states/sec generated+deduped"
+UNIT = "neighbours/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(layers, k, complete):
+    """Bytes the layer steps must move (per-step model B_r): read the frontier (8 F_r), write and
+    read back each candidate key (16 k F_r), read layers r and r-1 for the set difference
+    (8 (F_r + F_{r-1})), write the new layer (8 F_{r+1})."""
+    expanded = len(layers) if complete else len(layers) - 1
+    total = 0
+    for r in range(expanded):
+        F = layers[r]
+        Fm = layers[r - 1] if r > 0 else 0
+        Fp = layers[r + 1] if r + 1 < len(layers) else 0
+        total += 8 * F + 16 * k * F + 8 * (F + Fm) + 8 * Fp
+    return total
+
+
+def neighbours(layers, k, complete):
+    expanded = len(layers) if complete else len(layers) - 1
+    return k * sum(layers[:expanded])
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def get_workload(name):
+    if name == "s11_lrx":
+        return wl.config_s11_lrx()
+    if name == "s8_coxeter":
+        return wl.config_s8_coxeter()
+    if name == "s14_pancake":
+        return wl.config_s14_pancake()
+    raise ValueError(name)
+
+
+# --------------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+
+# Bounded samples of each workload for the oracle: the growth up to this radius (the oracle
+# expands layers 0..R-1).  About 10-20 s of one host core for S_11 LRX.
+ORACLE_SAMPLE_RADIUS = {"s11_lrx": 32, "s8_coxeter": -1, "s14_pancake": 6}
+REFERENCE_STEP_RADIUS = {"s11_lrx": 28, "s8_coxeter": -1, "s14_pancake": 5}
+
+
+def oracle_sample(job, radius):
+    import oracle
+    t0 = time.perf_counter()
+    layers, rc = oracle.growth(job.n, job.gens, max_radius=radius)
+    dt = time.perf_counter() - t0
+    complete = (rc == 0)
+    return neighbours(layers, job.k, complete), dt, layers, complete
+
+
+def cpu_baseline(wname, job):
+    R = ORACLE_SAMPLE_RADIUS.get(wname, -1)
+    nb, dt, layers, complete = oracle_sample(job, R)
+    return {"value": nb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{job.name}: growth to radius {len(layers) - 1} "
+                      f"({'complete' if complete else 'expanding layers 0..%d' % (len(layers) - 2)}), "
+                      f"{nb} neighbours in {dt:.2f} s, single-threaded unordered_set BFS",
+            "host_nproc": os.cpu_count()}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    job = get_workload(args.workload)
+    R = REFERENCE_STEP_RADIUS.get(args.workload, -1)
+    for _ in range(args.warmup):
+        oracle_sample(job, R)
+    total_nb, total_t = 0, 0.0
+    last = None
+    for _ in range(args.steps):
+        nb, dt, layers, complete = oracle_sample(job, R)
+        total_nb += nb
+        total_t += dt
+        last = (layers, complete)
+    value = total_nb / total_t
+    sample = (f"{job.name}: growth to radius {len(last[0]) - 1} per step "
+              f"({'complete' if last[1] else 'expanding layers 0..%d' % (len(last[0]) - 2)})")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "config": {"workload": job.name, "n": job.n, "k": job.k},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# --------------------------------------------------------------------------------------------
+# GPU arm
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2509_19162_gb300 as cg
+    cg.build()
+    from paper_2509_19162_gb300 import _cg  # noqa: F401  (load the library)
+
+    job = get_workload(args.workload)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    handle = cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
+                       stop_above=job.stop_above, keep_last=False)
+    # warm-up (also allocates the job's buffers: inputs resident before the timed region)
+    res = None
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            res = handle.run(stream)
+    complete = res.status == 0
+    layers = res.layers
+    nb_step = neighbours(layers, job.k, complete)
+    bytes_step = algorithmic_bytes(layers, job.k, complete)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(local) if rank == 0 or world == 1 else None
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms = 0.0
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()                               # evict L2 between timed steps
+        torch.cuda.synchronize()
+        ev[i][0].record(stream)
+        r = handle.run(stream)
+        ev[i][1].record(stream)
+        st = handle.stats()
+        kernel_ms += st["kernel_ms"]
+        launches += st["launches"]
+        if r.layers != layers:
+            raise RuntimeError("layer counts changed between steps")
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * nb_step * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public API: create + run + destroy with host inputs/outputs
+    e2e_times = []
+    h2d = d2h = 0
+    for i in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
+                       stop_above=job.stop_above) as g:
+            r = g.run(stream)
+            st = g.stats()
+        e2e_times.append(time.perf_counter() - t0)
+        h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+        if r.layers != layers:
+            raise RuntimeError("e2e layer counts differ")
+    e2e_value = world * nb_step / statistics.median(e2e_times)
+
+    peak, peak_kind = load_peaks()
+    kern_ms_per = kernel_ms / args.steps
+    achieved = bytes_step / (kern_ms_per / 1000.0) / 1e9
+    handle.close()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": job.name, "n": job.n, "k": job.k, "states": sum(layers),
+                   "layers": len(layers), "neighbours_per_step": nb_step,
+                   "strategy": "hash (visited table, persistent cooperative kernel)",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "hash_grow_kernel",
+                     "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
+                     "peak_source": peak_kind},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "api": "paper_2509_19162_gb300.Growth(...).run()"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, job)
+    print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="s11_lrx", choices=["s11_lrx", "s8_coxeter", "s14_pancake"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

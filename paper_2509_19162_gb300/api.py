@@ -1,0 +1,245 @@
+"""Python front end of the growth library (marshalling over the C ABI in _cg.py).
+
+    >>> from paper_2509_19162_gb300 import growth
+    >>> r = growth(8, coxeter_generators)          # runs on the current CUDA device
+    >>> r.layers[:4], r.diameter
+
+The computation is the growth of a permutation Cayley graph from the identity (Section 2.1,
+Def. "Growth"), run entirely by the library's CUDA kernels.  PyTorch is optional: a
+``torch.cuda.Stream`` may be passed as ``stream`` and ``use_torch_allocator()`` routes the
+library's device allocations through PyTorch's caching allocator.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _cg
+
+STRATEGIES = {"auto": _cg.CG_STRATEGY_AUTO, "hash": _cg.CG_STRATEGY_HASH, "sort": _cg.CG_STRATEGY_SORT}
+
+
+@dataclass
+class GrowthResult:
+    layers: List[int]
+    status: int
+
+    @property
+    def diameter(self) -> int:
+        return len(self.layers) - 1
+
+    @property
+    def complete(self) -> bool:
+        return self.status == _cg.CG_OK
+
+    @property
+    def total(self) -> int:
+        return int(sum(self.layers))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    h = getattr(stream, "cuda_stream", None)
+    if h is not None:
+        return int(h)
+    raise TypeError("stream must be None, an int handle or a torch.cuda.Stream")
+
+
+def _gens_bytes(n: int, gens: Sequence[Sequence[int]]) -> np.ndarray:
+    arr = np.asarray(gens, dtype=np.int64)
+    if arr.ndim != 2 or arr.shape[1] != n:
+        raise ValueError(f"gens must be k x {n}")
+    if arr.min(initial=0) < 0 or arr.max(initial=0) > 255:
+        raise ValueError("generator entries out of range")
+    return np.ascontiguousarray(arr.astype(np.uint8))
+
+
+def _is_inverse_closed(gens: Sequence[Sequence[int]]) -> bool:
+    s = {tuple(int(x) for x in g) for g in gens}
+    for g in s:
+        inv = [0] * len(g)
+        for i, v in enumerate(g):
+            inv[v] = i
+        if tuple(inv) not in s:
+            return False
+    return True
+
+
+class Growth:
+    """One growth job (cg_growth_create ... cg_growth_destroy)."""
+
+    def __init__(self, n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool] = None,
+                 max_radius: int = -1, mem_cap: int = 0, strategy: str = "auto",
+                 stop_above: int = 0, keep_last: bool = False):
+        g = _gens_bytes(n, gens)
+        if inverse_closed is None:
+            inverse_closed = _is_inverse_closed(gens)
+        self._gens = g
+        h = ctypes.c_void_p()
+        _cg.check(_cg.cg_growth_create(int(n), int(g.shape[0]),
+                                       g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                       int(bool(inverse_closed)), int(max_radius), int(mem_cap),
+                                       ctypes.byref(h)), "cg_growth_create")
+        self._h = h
+        self.n = n
+        self.k = g.shape[0]
+        if strategy not in STRATEGIES:
+            raise ValueError(f"strategy must be one of {sorted(STRATEGIES)}")
+        _cg.check(_cg.cg_growth_set_option(h, _cg.CG_OPT_STRATEGY, STRATEGIES[strategy]),
+                  "cg_growth_set_option(strategy)")
+        if stop_above:
+            _cg.check(_cg.cg_growth_set_option(h, _cg.CG_OPT_STOP_ABOVE, int(stop_above)),
+                      "cg_growth_set_option(stop_above)")
+        if keep_last:
+            _cg.check(_cg.cg_growth_set_option(h, _cg.CG_OPT_KEEP_LAST, 1),
+                      "cg_growth_set_option(keep_last)")
+        self._cap = 1024
+        self._out = np.zeros(self._cap, dtype=np.uint64)
+
+    @property
+    def order(self) -> int:
+        return int(_cg.cg_growth_group_order(self._h))
+
+    def run(self, stream=None) -> GrowthResult:
+        nl = ctypes.c_int(0)
+        while True:
+            rc = _cg.cg_growth_run(self._h, _stream_handle(stream),
+                                   self._out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   self._cap, ctypes.byref(nl))
+            if rc == _cg.CG_EINVAL and nl.value > self._cap:
+                self._cap = nl.value
+                self._out = np.zeros(self._cap, dtype=np.uint64)
+                continue
+            break
+        _cg.check(rc, "cg_growth_run")
+        return GrowthResult([int(x) for x in self._out[:nl.value]], rc)
+
+    def stats(self) -> dict:
+        st = _cg.cg_growth_stats()
+        _cg.check(_cg.cg_growth_get_stats(self._h, ctypes.byref(st)), "cg_growth_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def last_layer(self) -> np.ndarray:
+        cnt = ctypes.c_uint64(0)
+        _cg.cg_growth_last_layer(self._h, None, 0, ctypes.byref(cnt))
+        out = np.zeros(max(1, cnt.value), dtype=np.uint64)
+        _cg.check(_cg.cg_growth_last_layer(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                           cnt.value, ctypes.byref(cnt)), "cg_growth_last_layer")
+        return out[:cnt.value]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _cg.cg_growth_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def growth(n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool] = None,
+           max_radius: int = -1, mem_cap: int = 0, strategy: str = "auto", stop_above: int = 0,
+           stream=None) -> GrowthResult:
+    """Growth vector |S_0|, |S_1|, ... of the Cayley graph of <gens> from the identity."""
+    with Growth(n, gens, inverse_closed, max_radius, mem_cap, strategy, stop_above) as g:
+        return g.run(stream)
+
+
+class Batch:
+    """Many independent growth jobs run together (cg_batch_create ... cg_batch_destroy)."""
+
+    def __init__(self, jobs, mem_cap: int = 0):
+        """jobs: sequence of (n, gens, inverse_closed, max_radius)."""
+        self.njobs = len(jobs)
+        ns = np.array([j[0] for j in jobs], dtype=np.int32)
+        ks = np.array([len(j[1]) for j in jobs], dtype=np.int32)
+        blobs = [_gens_bytes(j[0], j[1]).ravel() for j in jobs]
+        offs = np.zeros(self.njobs, dtype=np.uint64)
+        if self.njobs:
+            offs[1:] = np.cumsum([b.size for b in blobs])[:-1]
+        flat = np.ascontiguousarray(np.concatenate(blobs) if blobs else np.zeros(1, np.uint8))
+        inv = np.array([int(bool(j[2])) for j in jobs], dtype=np.int32)
+        rad = np.array([int(j[3]) for j in jobs], dtype=np.int32)
+        self._keep = (ns, ks, flat, offs, inv, rad)
+        h = ctypes.c_void_p()
+        ip = ctypes.POINTER(ctypes.c_int)
+        _cg.check(_cg.cg_batch_create(self.njobs, ns.ctypes.data_as(ip), ks.ctypes.data_as(ip),
+                                      flat.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                      offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      inv.ctypes.data_as(ip), rad.ctypes.data_as(ip), int(mem_cap),
+                                      ctypes.byref(h)), "cg_batch_create")
+        self._h = h
+
+    def run(self, stream=None, cap: int = 512) -> List[GrowthResult]:
+        out = np.zeros(self.njobs * cap, dtype=np.uint64)
+        nl = np.zeros(self.njobs, dtype=np.int32)
+        stv = np.zeros(self.njobs, dtype=np.int32)
+        ip = ctypes.POINTER(ctypes.c_int)
+        rc = _cg.cg_batch_run(self._h, _stream_handle(stream),
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
+                              nl.ctypes.data_as(ip), stv.ctypes.data_as(ip))
+        _cg.check(rc, "cg_batch_run")
+        res = []
+        for j in range(self.njobs):
+            res.append(GrowthResult([int(x) for x in out[j * cap: j * cap + nl[j]]], int(stv[j])))
+        return res
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _cg.cg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_torch_alloc_refs = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _torch_alloc_refs
+    if not enable:
+        _cg.check(_cg.cg_set_allocator(_cg.ALLOC_FN(), _cg.FREE_FN(), None), "cg_set_allocator")
+        _torch_alloc_refs = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _cg.ALLOC_FN(_alloc), _cg.FREE_FN(_free)
+    _torch_alloc_refs = (a, f)
+    _cg.check(_cg.cg_set_allocator(a, f, None), "cg_set_allocator")

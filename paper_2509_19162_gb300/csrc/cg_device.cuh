@@ -1,0 +1,125 @@
+// Device-side building blocks of the growth kernels: the generator action on packed keys,
+// the key hash, the open-addressing insert, and a bounded grid-wide barrier.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cg_internal.h"
+#include "../../include/cg_growth.h"
+
+namespace cg {
+
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, unsigned r) {
+    return (x << r) | (x >> ((64u - r) & 63u));
+}
+
+// t[i] = s[g[i]] on 4-bit packed keys, as a union of rotated, masked copies of s.
+__device__ __forceinline__ uint64_t apply_gen(const GenSM& g, uint64_t s) {
+    uint64_t t = 0;
+    const uint32_t nt = g.nterms;
+#pragma unroll 4
+    for (uint32_t i = 0; i < nt; ++i) t |= rotl64(s, g.rot[i]) & g.mask[i];
+    return t;
+}
+
+// 64-bit finaliser of MurmurHash3 (A. Appleby, public domain): a bijection of uint64.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Relaxed load served by L2 (never a stale L1 line): used for data other SMs write.
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_ull(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Insert-if-absent with linear probing.  Returns 1 if this call inserted the key, 0 if it was
+// present (or inserted concurrently by another thread), -1 if `max_probe` slots were visited
+// without finding the key or an empty slot.
+__device__ __forceinline__ int table_insert(uint64_t* table, uint64_t mask, uint64_t key,
+                                            uint64_t max_probe) {
+    uint64_t h = mix64(key) & mask;
+    for (uint64_t p = 0; p < max_probe; ++p) {
+        uint64_t cur = ld_relaxed(table + h);
+        if (cur == key) return 0;
+        if (cur == kEmpty) {
+            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(table + h),
+                                                (unsigned long long)kEmpty,
+                                                (unsigned long long)key);
+            if (prev == kEmpty) return 1;
+            if (prev == key) return 0;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Waits are bounded by
+// `timeout_ns` of wall time; on timeout the error word is set to CG_ETIMEOUT and false is
+// returned, as it is when another block has already set the error word.  Callers return
+// from the kernel on false.
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, uint64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &ctl->bar_gen;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (*vgen == gen) {
+                if (*(volatile int*)&ctl->err != 0) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicCAS(&ctl->err, 0, CG_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)&ctl->err != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace cg

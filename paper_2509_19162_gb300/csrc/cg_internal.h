@@ -1,0 +1,66 @@
+// Internal types shared by the host driver and the kernels of the growth library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cg {
+
+constexpr uint64_t kEmpty = ~0ull;   // empty hash slot: never a valid permutation key, n >= 2
+constexpr int kMaxN = 16;
+constexpr int kMaxLayers = 16384;    // device layer-size array per job
+
+// A generator in shift-and-mask form.  The gather t[i] = s[g[i]] moves nibble g[i] to nibble
+// i, a rotation of the packed key by 4*(i - g[i]) bits.  Positions sharing one offset form one
+// term: t = OR_t rotl(s, rot[t]) & mask[t].  Cyclic shifts need 2 terms, adjacent
+// transpositions 3, a prefix reversal of length j needs j+1 at most, any generator <= n.
+struct GenSM {
+    uint32_t nterms;
+    uint32_t pad;
+    uint8_t rot[kMaxN];
+    uint64_t mask[kMaxN];
+};
+
+enum JobStatus : int {
+    kRunning = 0,
+    kDone = 1,          // empty next layer: growth complete
+    kTruncRadius = 2,   // reached max_radius (or the layer array's capacity)
+    kTruncAbove = 3,    // recorded the first layer larger than stop_above
+    kNeedMem = 4,       // the layer being built did not fit; layers up to `radius` are exact
+    kDeviceError = 5,
+};
+
+// One growth job of the hash strategy as the persistent kernel sees it.
+struct JobDev {
+    // static, written by the host
+    uint64_t* keys;            // all layers back to back; layer r = keys[off_r, off_{r+1})
+    uint64_t keys_cap;
+    uint64_t* table;           // visited set, table_mask + 1 slots
+    uint64_t table_mask;
+    const GenSM* gens;         // k entries
+    uint64_t* layer_sizes;     // device, layers_cap entries; [0] = 1
+    uint64_t stop_above;       // 0: none
+    int k;
+    int n;
+    int layers_cap;
+    int max_radius;            // < 0: unlimited
+    // dynamic, updated between rounds by block 0
+    unsigned long long lo;     // frontier = keys[lo, hi)
+    unsigned long long hi;
+    unsigned long long tail;   // append cursor (atomic during a round)
+    int radius;                // radius of the frontier layer
+    int status;                // JobStatus
+    int overflow;              // set during a round: keys or table ran out
+    int pad;
+};
+
+// Control block of the persistent kernel (device memory, zero-initialised by the host).
+struct Ctl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int err;                        // 0, or a CG_E* code set by a kernel
+    int rounds;                     // rounds completed
+    unsigned long long total_units; // warp work units of the current round
+};
+
+}  // namespace cg

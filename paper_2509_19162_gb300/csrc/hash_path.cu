@@ -1,0 +1,309 @@
+// Hash strategy of the growth library: every layer step of every job in one persistent,
+// cooperative launch.
+//
+// One round = one BFS layer step (Section 3.1.2) for every running job:
+//   phase A  (all warps)  for each (job, generator, 32 frontier states):  t = g(s)  [expand],
+//            insert-if-absent of t into the job's visited table  [dedup + visited probe],
+//            warp-aggregated append of the winners to the job's key array  [compaction];
+//   barrier
+//   phase B  (block 0)    per job: |L_{r+1}| = tail - hi  [layer count], stop tests, and the
+//            exclusive scan of next-round work units over jobs;
+//   barrier.
+// The visited table holds every state seen so far, which is what a directed generating set
+// needs; for an inverse-closed set it is a superset of the two layers that suffice.
+#include <cooperative_groups.h>
+#include <cstdio>
+
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+namespace cg {
+
+namespace {
+
+constexpr int kGrowBlock = 256;
+constexpr uint64_t kMaxProbe = 1ull << 16;
+
+// Largest j with ubeg[j] <= u (ubeg ascending, ubeg[0] = 0).
+__device__ __forceinline__ int find_job(const unsigned long long* ubeg, int njobs,
+                                        unsigned long long u) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ld_relaxed_ull(ubeg + mid) <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Phase B, executed by block 0 only: close the layer of every running job and lay out the
+// work of the next round.  ubeg has njobs + 1 entries.
+__device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl) {
+    __shared__ unsigned long long s_warp[kGrowBlock / 32];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < njobs; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        unsigned long long units = 0;
+        if (j < njobs) {
+            JobDev& J = jobs[j];
+            if (J.status == kRunning) {
+                // tail and overflow are updated with atomics by every block: read them from L2.
+                const unsigned long long tail = ld_relaxed_ull(&J.tail);
+                if (ld_relaxed_int(&J.overflow)) {
+                    J.status = kNeedMem;
+                } else {
+                    const unsigned long long fresh = tail - J.hi;
+                    if (fresh == 0) {
+                        J.status = kDone;
+                    } else {
+                        const int r = J.radius + 1;
+                        J.layer_sizes[r] = fresh;
+                        J.radius = r;
+                        J.lo = J.hi;
+                        J.hi = tail;
+                        if (J.max_radius >= 0 && r >= J.max_radius) J.status = kTruncRadius;
+                        else if (J.stop_above > 0 && fresh > J.stop_above) J.status = kTruncAbove;
+                        else if (r + 1 >= J.layers_cap) J.status = kTruncRadius;
+                    }
+                }
+                if (J.status == kRunning)
+                    units = (unsigned long long)J.k * ((J.hi - J.lo + 31) >> 5);
+            }
+        }
+        // block-wide exclusive scan of units
+        unsigned long long v = units;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += n;
+        }
+        if (lane == 31) s_warp[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long w = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long n = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += n;
+            }
+            if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long before = (wid ? s_warp[wid - 1] : 0) + (v - units) + s_carry;
+        if (j < njobs) ubeg[j] = before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = before + units;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ubeg[njobs] = s_carry;
+        ctl->total_units = s_carry;
+        ctl->rounds += 1;
+    }
+}
+
+__global__ void __launch_bounds__(kGrowBlock)
+hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
+                 uint64_t timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
+
+    for (int round = 0; round < max_rounds; ++round) {
+        const unsigned long long total = ld_relaxed_ull(&ctl->total_units);
+        if (total == 0) break;
+
+        for (unsigned long long u = warp0; u < total; u += nwarps) {
+            const int j = njobs == 1 ? 0 : find_job(ubeg, njobs, u);
+            JobDev* J = jobs + j;
+            if (ld_relaxed_int(&J->overflow)) continue;
+            const unsigned long long lo = ld_relaxed_ull(&J->lo);
+            const unsigned long long hi = ld_relaxed_ull(&J->hi);
+            const unsigned long long nblk = (hi - lo + 31) >> 5;
+            const unsigned long long local = u - ld_relaxed_ull(ubeg + j);
+            const unsigned g = (unsigned)(local / nblk);
+            const unsigned long long idx = lo + ((local - g * nblk) << 5) + lane;
+            uint64_t* keys = J->keys;
+            int ins = 0;
+            uint64_t t = 0;
+            if (idx < hi) {
+                const uint64_t s = __ldcg(keys + idx);
+                t = apply_gen(J->gens[g], s);
+                ins = table_insert(J->table, J->table_mask, t, kMaxProbe);
+            }
+            const unsigned fresh = __ballot_sync(0xffffffffu, ins == 1);
+            if (__any_sync(0xffffffffu, ins < 0)) {
+                if (lane == 0) atomicExch(&J->overflow, 1);
+            }
+            if (fresh) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&J->tail, (unsigned long long)__popc(fresh));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (ins == 1) {
+                    const unsigned long long pos = base + __popc(fresh & lanemask_lt());
+                    if (pos < J->keys_cap) keys[pos] = t;
+                    else atomicExch(&J->overflow, 1);
+                }
+            }
+        }
+        if (!grid_barrier(ctl, timeout_ns)) return;
+        if (blockIdx.x == 0) close_round(jobs, njobs, ubeg, ctl);
+        if (!grid_barrier(ctl, timeout_ns)) return;
+    }
+}
+
+// Set up job j for a run from the identity: the table must already be cleared.
+__global__ void init_jobs_kernel(JobDev* jobs, int njobs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= njobs) return;
+    JobDev& J = jobs[j];
+    uint64_t id = 0;
+    for (int i = 0; i < J.n; ++i) id |= (uint64_t)i << (4 * i);
+    J.keys[0] = id;
+    table_insert(J.table, J.table_mask, id, kMaxProbe);
+    J.layer_sizes[0] = 1;
+    J.lo = 0;
+    J.hi = 1;
+    J.tail = 1;
+    J.radius = 0;
+    J.overflow = 0;
+    J.status = kRunning;
+    if (J.max_radius == 0) J.status = kTruncRadius;
+}
+
+// Work layout of the first round (after init, or after the host resized a job's buffers):
+// k warp units per 32 frontier states of every running job.
+__global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    unsigned long long acc = 0;
+    for (int j = 0; j < njobs; ++j) {
+        ubeg[j] = acc;
+        if (jobs[j].status == kRunning)
+            acc += (unsigned long long)jobs[j].k * ((jobs[j].hi - jobs[j].lo + 31) >> 5);
+    }
+    ubeg[njobs] = acc;
+    ctl->total_units = acc;
+    ctl->rounds = 0;
+    ctl->bar_count = 0;
+    ctl->bar_gen = 0;
+    ctl->err = 0;
+}
+
+// Re-insert keys[0, count) of one job into its (cleared) table; used after the key array
+// grew.  Dups cannot occur: the keys are distinct.
+__global__ void rebuild_table_kernel(const uint64_t* keys, unsigned long long count,
+                                     uint64_t* table, uint64_t mask, int* err) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         i < count; i += (unsigned long long)gridDim.x * blockDim.x) {
+        if (table_insert(table, mask, __ldcg(keys + i), kMaxProbe) < 0) atomicExch(err, CG_EDEVICE);
+    }
+}
+
+__global__ void expand_kernel(const GenSM* __restrict__ gens, int k, const uint64_t* __restrict__ in,
+                              unsigned long long F, uint64_t* __restrict__ out) {
+    const unsigned long long total = F * (unsigned long long)k;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned g = (unsigned)(i / F);
+        const unsigned long long s = i - (unsigned long long)g * F;
+        out[i] = apply_gen(gens[g], in[s]);
+    }
+}
+
+__global__ void hash_insert_kernel(uint64_t* table, uint64_t mask, const uint64_t* __restrict__ keys,
+                                   unsigned long long N, uint64_t* out,
+                                   unsigned long long* count, int* fail) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = stride >> 5;
+    for (unsigned long long w = warp; (w << 5) < N; w += nw) {
+        const unsigned long long idx = (w << 5) + lane;
+        int ins = 0;
+        uint64_t t = 0;
+        if (idx < N) {
+            t = keys[idx];
+            ins = table_insert(table, mask, t, mask + 1);
+        }
+        if (__any_sync(0xffffffffu, ins < 0) && lane == 0) atomicExch(fail, 1);
+        const unsigned fresh = __ballot_sync(0xffffffffu, ins == 1);
+        if (fresh) {
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(fresh));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (ins == 1) out[b + __popc(fresh & lanemask_lt())] = t;
+        }
+    }
+}
+
+__global__ void finish_insert_count_kernel(unsigned long long* count, const int* fail) {
+    if (*fail) *count = ~0ull;
+}
+
+}  // namespace
+
+int hash_grow_block() { return kGrowBlock; }
+
+int hash_grow_max_grid(int device) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hash_grow_kernel, kGrowBlock, 0) !=
+        cudaSuccess)
+        return 0;
+    return sms * per_sm;
+}
+
+cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
+                             cudaStream_t st) {
+    init_jobs_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs);
+    init_units_kernel<<<1, 1, 0, st>>>(d_jobs, njobs, d_ubeg, d_ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
+                                cudaStream_t st) {
+    init_units_kernel<<<1, 1, 0, st>>>(d_jobs, njobs, d_ubeg, d_ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
+                             int grid, int max_rounds, uint64_t timeout_ns, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kGrowBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, hash_grow_kernel, d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
+                              timeout_ns);
+}
+
+cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,
+                                 uint64_t mask, int* d_err, int grid, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    rebuild_table_kernel<<<grid, 256, 0, st>>>(keys, count, table, mask, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,
+                          uint64_t* out, int grid, cudaStream_t st) {
+    if (F == 0) return cudaSuccess;
+    expand_kernel<<<grid, 256, 0, st>>>(d_gens, k, in, F, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash_insert(uint64_t* table, uint64_t mask, const uint64_t* keys,
+                               unsigned long long N, uint64_t* out, unsigned long long* count,
+                               int* fail, int grid, cudaStream_t st) {
+    hash_insert_kernel<<<grid, 256, 0, st>>>(table, mask, keys, N, out, count, fail);
+    finish_insert_count_kernel<<<1, 1, 0, st>>>(count, fail);
+    return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,740 @@
+// Host driver and C ABI of the growth library (declarations and contracts in
+// include/cg_growth.h).
+//
+// A growth job (Section 2.1, Def. "Growth") is run by the hash strategy: one persistent,
+// cooperative kernel launch performs every layer step (hash_path.cu).  The host only plans
+// device memory, uploads the job, and reads the layer sizes back.  When a layer outgrows the
+// job's buffers the kernel stops at the last complete layer; the host then grows the buffers
+// (within mem_cap), rebuilds the visited table from the stored states and relaunches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "../../include/cg_growth.h"
+#include "cg_internal.h"
+#include "cg_kernels.h"
+#include "group_order.h"
+
+using cg::Ctl;
+using cg::GenSM;
+using cg::JobDev;
+
+namespace {
+
+constexpr uint64_t kDefaultMemCap = 160ull << 30;
+constexpr uint64_t kTimeoutNs = 30ull * 1000 * 1000 * 1000;  // per barrier wait
+constexpr double kMaxLoad = 0.75;                               // visited-table load limit
+constexpr uint64_t kExactAllocLimit = 24ull << 30;  // allocate |<S>| states up front below this
+
+// ---- allocator ------------------------------------------------------------------------
+struct Allocator {
+    cg_alloc_fn alloc = nullptr;
+    cg_free_fn free_fn = nullptr;
+    void* ctx = nullptr;
+} g_alloc;
+
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t pool_for(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&g_pool[dev], &props) != cudaSuccess) {
+            cudaGetLastError();
+            g_pool[dev] = nullptr;
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return g_pool[dev];
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (g_alloc.alloc) return g_alloc.alloc(bytes, st, g_alloc.ctx);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    cudaMemPool_t pool = pool_for(dev);
+    if (!pool) return nullptr;
+    void* p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (!p) return;
+    if (g_alloc.free_fn) g_alloc.free_fn(p, st, g_alloc.ctx);
+    else cudaFreeAsync(p, st);
+}
+
+// ---- generators -------------------------------------------------------------------------
+bool is_perm_row(const uint8_t* g, int n) {
+    unsigned seen = 0;
+    for (int i = 0; i < n; ++i) {
+        if (g[i] >= n || (seen >> g[i]) & 1u) return false;
+        seen |= 1u << g[i];
+    }
+    return true;
+}
+
+bool is_identity_row(const uint8_t* g, int n) {
+    for (int i = 0; i < n; ++i)
+        if (g[i] != i) return false;
+    return true;
+}
+
+// Shift-and-mask form of the gather t[i] = s[g[i]] (see GenSM).
+GenSM make_gensm(const uint8_t* g, int n) {
+    GenSM G;
+    std::memset(&G, 0, sizeof(G));
+    for (int i = 0; i < n; ++i) {
+        const unsigned rot = (unsigned)((4 * (i - (int)g[i]) + 64) & 63);
+        uint32_t t = 0;
+        while (t < G.nterms && G.rot[t] != rot) ++t;
+        if (t == G.nterms) {
+            G.rot[t] = (uint8_t)rot;
+            G.nterms++;
+        }
+        G.mask[t] |= 0xFull << (4 * i);
+    }
+    return G;
+}
+
+// Distinct non-identity rows.
+std::vector<std::vector<uint8_t>> clean_rows(int n, int k, const uint8_t* gens) {
+    std::set<std::vector<uint8_t>> seen;
+    std::vector<std::vector<uint8_t>> out;
+    for (int j = 0; j < k; ++j) {
+        std::vector<uint8_t> r(gens + (size_t)j * n, gens + (size_t)(j + 1) * n);
+        if (is_identity_row(r.data(), n)) continue;
+        if (seen.insert(r).second) out.push_back(r);
+    }
+    return out;
+}
+
+bool closed_under_inverse(const std::vector<std::vector<uint8_t>>& rows, int n) {
+    std::set<std::vector<uint8_t>> s(rows.begin(), rows.end());
+    for (auto& r : rows) {
+        std::vector<uint8_t> inv(n);
+        for (int i = 0; i < n; ++i) inv[r[i]] = (uint8_t)i;
+        if (!s.count(inv)) return false;
+    }
+    return true;
+}
+
+int validate(int n, int k, const uint8_t* gens) {
+    if (n < 1 || n > cg::kMaxN || k < 1 || gens == nullptr) return CG_EINVAL;
+    for (int j = 0; j < k; ++j)
+        if (!is_perm_row(gens + (size_t)j * n, n)) return CG_EINVAL;
+    return CG_OK;
+}
+
+uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+uint64_t table_slots_for(uint64_t cap) {
+    return std::max<uint64_t>(1024, next_pow2((uint64_t)((double)cap / kMaxLoad) + 1));
+}
+
+uint64_t bytes_for(uint64_t cap) { return cap * 8 + table_slots_for(cap) * 8; }
+
+// Largest state capacity whose keys + table fit in `mem` bytes.
+uint64_t max_cap_for_mem(uint64_t mem) {
+    uint64_t best = 0;
+    for (int p = 10; p <= 42; ++p) {
+        const uint64_t slots = 1ull << p;
+        if (slots * 8 >= mem) break;
+        const uint64_t by_load = (uint64_t)((double)slots * kMaxLoad) - 1;
+        const uint64_t by_mem = (mem - slots * 8) / 8;
+        best = std::max(best, std::min(by_load, by_mem));
+    }
+    return best;
+}
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return CG_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA;
+}
+
+int status_to_rc(int status) {
+    switch (status) {
+        case cg::kDone: return CG_OK;
+        case cg::kTruncRadius: return CG_TRUNC_RADIUS;
+        case cg::kTruncAbove: return CG_TRUNC_ABOVE;
+        case cg::kNeedMem: return CG_TRUNC_MEMCAP;
+        case cg::kRunning: return CG_EDEVICE;
+        default: return CG_EDEVICE;
+    }
+}
+
+int device_grid_cache[64] = {};
+
+int grow_grid(int dev) {
+    if (dev < 0 || dev >= 64) return 0;
+    if (!device_grid_cache[dev]) device_grid_cache[dev] = cg::hash_grow_max_grid(dev);
+    return device_grid_cache[dev];
+}
+
+}  // namespace
+
+// ---- single job ---------------------------------------------------------------------------
+struct cg_growth {
+    int n = 0;
+    int k = 0;                                   // distinct non-identity generators
+    std::vector<GenSM> gsm;
+    int inverse_closed = 0;
+    int max_radius = -1;
+    uint64_t mem_cap = kDefaultMemCap;
+    int strategy = CG_STRATEGY_AUTO;
+    uint64_t stop_above = 0;
+    int keep_last = 0;
+    uint64_t order = 1;
+    int device = -1;
+    cudaStream_t alloc_stream = nullptr;
+
+    GenSM* d_gens = nullptr;
+    JobDev* d_job = nullptr;
+    Ctl* d_ctl = nullptr;
+    unsigned long long* d_ubeg = nullptr;
+    uint64_t* d_layers = nullptr;
+    uint64_t* d_keys = nullptr;
+    uint64_t keys_cap = 0;
+    uint64_t* d_table = nullptr;
+    uint64_t table_slots = 0;
+
+    JobDev host_job{};
+    bool have_last = false;
+    cg_growth_stats stats{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    void release(cudaStream_t st) {
+        dev_free(d_gens, st);
+        dev_free(d_job, st);
+        dev_free(d_ctl, st);
+        dev_free(d_ubeg, st);
+        dev_free(d_layers, st);
+        dev_free(d_keys, st);
+        dev_free(d_table, st);
+        d_gens = nullptr; d_job = nullptr; d_ctl = nullptr; d_ubeg = nullptr;
+        d_layers = nullptr; d_keys = nullptr; d_table = nullptr;
+        keys_cap = table_slots = 0;
+    }
+};
+
+namespace {
+
+int ensure_small_buffers(cg_growth* h, cudaStream_t st) {
+    if (h->d_job) return CG_OK;
+    h->d_gens = (GenSM*)dev_alloc(sizeof(GenSM) * std::max(1, h->k), st);
+    h->d_job = (JobDev*)dev_alloc(sizeof(JobDev), st);
+    h->d_ctl = (Ctl*)dev_alloc(sizeof(Ctl), st);
+    h->d_ubeg = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 2, st);
+    h->d_layers = (uint64_t*)dev_alloc(sizeof(uint64_t) * cg::kMaxLayers, st);
+    if (!h->d_gens || !h->d_job || !h->d_ctl || !h->d_ubeg || !h->d_layers) return CG_ENOMEM;
+    if (h->k > 0) {
+        cudaError_t e = cudaMemcpyAsync(h->d_gens, h->gsm.data(), sizeof(GenSM) * h->k,
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_rc(e);
+    }
+    return CG_OK;
+}
+
+// (Re)allocate keys + table for `cap` states, keeping the first `keep` keys.
+int resize_state(cg_growth* h, uint64_t cap, uint64_t keep, cudaStream_t st) {
+    uint64_t* keys = (uint64_t*)dev_alloc(cap * 8, st);
+    if (!keys) return CG_ENOMEM;
+    const uint64_t slots = table_slots_for(cap);
+    uint64_t* table = (uint64_t*)dev_alloc(slots * 8, st);
+    if (!table) { dev_free(keys, st); return CG_ENOMEM; }
+    if (keep > 0) {
+        cudaError_t e = cudaMemcpyAsync(keys, h->d_keys, keep * 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { dev_free(keys, st); dev_free(table, st); return cuda_rc(e); }
+    }
+    dev_free(h->d_keys, st);
+    dev_free(h->d_table, st);
+    h->d_keys = keys;
+    h->d_table = table;
+    h->keys_cap = cap;
+    h->table_slots = slots;
+    return CG_OK;
+}
+
+void fill_static(cg_growth* h, JobDev& J) {
+    J.keys = h->d_keys;
+    J.keys_cap = h->keys_cap;
+    J.table = h->d_table;
+    J.table_mask = h->table_slots - 1;
+    J.gens = h->d_gens;
+    J.layer_sizes = h->d_layers;
+    J.stop_above = h->stop_above;
+    J.k = h->k;
+    J.n = h->n;
+    J.layers_cap = cg::kMaxLayers;
+    J.max_radius = h->max_radius;
+}
+
+int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
+    const bool fresh_alloc = (h->d_job == nullptr);
+    int rc = ensure_small_buffers(h, st);
+    if (rc) return rc;
+    if (fresh_alloc) h->stats.h2d_bytes += sizeof(GenSM) * h->k;
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    const uint64_t max_cap = std::min<uint64_t>(h->order, max_cap_for_mem(mem > (1 << 20) ? mem - (1 << 20) : mem));
+    if (max_cap < 1) return CG_ENOMEM;
+    if (!h->d_keys) {
+        uint64_t start = h->order;
+        if (bytes_for(start) > std::min<uint64_t>(mem, kExactAllocLimit))
+            start = std::min<uint64_t>(max_cap, 1ull << 24);
+        start = std::min(start, max_cap);
+        rc = resize_state(h, std::max<uint64_t>(start, 1), 0, st);
+        if (rc) return rc;
+    }
+    const int grid_max = grow_grid(h->device);
+    if (grid_max <= 0) return CG_ECUDA;
+    // Small groups finish faster with fewer blocks at each barrier.
+    const uint64_t want = (h->order * (uint64_t)std::max(1, h->k)) / (32 * 8 * 4) + 1;
+    const int grid = (int)std::min<uint64_t>((uint64_t)grid_max, std::max<uint64_t>(want, 1));
+
+    cudaError_t e = cudaMemsetAsync(h->d_table, 0xFF, h->table_slots * 8, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    JobDev J;
+    std::memset(&J, 0, sizeof(J));
+    fill_static(h, J);
+    if ((e = cudaMemcpyAsync(h->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cg::launch_init_jobs(h->d_job, 1, h->d_ubeg, h->d_ctl, st)) != cudaSuccess)
+        return cuda_rc(e);
+    h->stats.launches += 2;  // init_jobs + init_units
+    h->stats.h2d_bytes += sizeof(J);
+    if (!h->ev0) {
+        if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
+    }
+    for (;;) {
+        if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cg::launch_hash_grow(h->d_job, 1, h->d_ubeg, h->d_ctl, grid, cg::kMaxLayers + 1,
+                                      kTimeoutNs, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.launches += 1;
+        Ctl ctl;
+        if ((e = cudaMemcpyAsync(&J, h->d_job, sizeof(J), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(&ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.d2h_bytes += sizeof(J) + sizeof(ctl);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->stats.kernel_ms += ms;
+        h->stats.rounds += ctl.rounds;
+        if (ctl.err) return ctl.err;
+        if (J.status != cg::kNeedMem) break;
+        if (h->keys_cap >= max_cap) break;  // cannot grow: truncated by mem_cap
+        // Grow: keep layers 0..radius (keys[0, hi)), rebuild the visited table from them.
+        const uint64_t keep = J.hi;
+        const uint64_t newcap = std::min<uint64_t>(max_cap, std::max<uint64_t>(h->keys_cap * 4, keep + 1));
+        if ((rc = resize_state(h, newcap, keep, st))) return rc;
+        if ((e = cudaMemsetAsync(h->d_table, 0xFF, h->table_slots * 8, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cg::launch_rebuild_table(h->d_keys, keep, h->d_table, h->table_slots - 1,
+                                          &h->d_ctl->err, grid_max, st)) != cudaSuccess)
+            return cuda_rc(e);
+        fill_static(h, J);
+        J.tail = J.hi;
+        J.overflow = 0;
+        J.status = cg::kRunning;
+        if ((e = cudaMemcpyAsync(h->d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cg::launch_resume_units(h->d_job, 1, h->d_ubeg, h->d_ctl, st)) != cudaSuccess)
+            return cuda_rc(e);
+        h->stats.launches += 2;  // rebuild_table + init_units
+        h->stats.h2d_bytes += sizeof(J);
+    }
+    h->stats.state_capacity = h->keys_cap;
+    h->stats.table_slots = h->table_slots;
+    h->host_job = J;
+    *final_status = J.status;
+    return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_set_allocator(cg_alloc_fn alloc, cg_free_fn free_fn, void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return CG_EINVAL;
+    g_alloc.alloc = alloc;
+    g_alloc.free_fn = free_fn;
+    g_alloc.ctx = ctx;
+    return CG_OK;
+}
+
+int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
+                     uint64_t mem_cap, cg_growth_t* out) {
+    if (out == nullptr) return CG_EINVAL;
+    *out = nullptr;
+    int rc = validate(n, k, gens);
+    if (rc) return rc;
+    auto rows = clean_rows(n, k, gens);
+    if (inverse_closed && !closed_under_inverse(rows, n)) return CG_ENOTCLOSED;
+    cg_growth* h = new (std::nothrow) cg_growth();
+    if (!h) return CG_ENOMEM;
+    h->n = n;
+    h->k = (int)rows.size();
+    for (auto& r : rows) h->gsm.push_back(make_gensm(r.data(), n));
+    h->inverse_closed = inverse_closed ? 1 : 0;
+    h->max_radius = max_radius < 0 ? -1 : max_radius;
+    h->mem_cap = mem_cap ? mem_cap : kDefaultMemCap;
+    std::vector<uint8_t> flat;
+    for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
+    h->order = rows.empty() ? 1 : cg::group_order(n, (int)rows.size(), flat.data());
+    *out = h;
+    return CG_OK;
+}
+
+int cg_growth_set_option(cg_growth_t h, int option, int64_t value) {
+    if (!h) return CG_EINVAL;
+    switch (option) {
+        case CG_OPT_STRATEGY:
+            if (value < CG_STRATEGY_AUTO || value > CG_STRATEGY_SORT) return CG_EINVAL;
+            if (value == CG_STRATEGY_SORT && !h->inverse_closed) return CG_EINVAL;
+            h->strategy = (int)value;
+            return CG_OK;
+        case CG_OPT_STOP_ABOVE:
+            if (value < 0) return CG_EINVAL;
+            h->stop_above = (uint64_t)value;
+            return CG_OK;
+        case CG_OPT_KEEP_LAST:
+            h->keep_last = value ? 1 : 0;
+            return CG_OK;
+        default:
+            return CG_EINVAL;
+    }
+}
+
+int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, int cap,
+                  int* num_layers_out) {
+    if (!h || !layer_sizes_out || !num_layers_out || cap < 0) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    h->have_last = false;
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    if (h->k == 0 || h->max_radius == 0) {  // trivial group or radius 0: only the identity
+        *num_layers_out = 1;
+        if (cap < 1) return CG_EINVAL;
+        layer_sizes_out[0] = 1;
+        return h->k == 0 ? CG_OK : CG_TRUNC_RADIUS;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if (h->device >= 0 && h->device != dev) return CG_EINVAL;
+    h->device = dev;
+    int status = 0;
+    int rc = run_hash(h, st, &status);
+    if (rc) return rc;
+    const int layers = h->host_job.radius + 1;
+    *num_layers_out = layers;
+    if (cap < layers) return CG_EINVAL;
+    e = cudaMemcpyAsync(layer_sizes_out, h->d_layers, sizeof(uint64_t) * layers,
+                        cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+    h->stats.d2h_bytes += sizeof(uint64_t) * layers;
+    h->have_last = true;
+    return status_to_rc(status);
+}
+
+int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64_t* count_out) {
+    if (!h || !count_out || !h->have_last) return CG_EINVAL;
+    const uint64_t lo = h->host_job.lo, hi = h->host_job.hi;
+    *count_out = hi - lo;
+    if (cap < hi - lo || (!keys_out && hi > lo)) return CG_EINVAL;
+    cudaError_t e = cudaMemcpy(keys_out, h->d_keys + lo, (hi - lo) * 8, cudaMemcpyDeviceToHost);
+    return cuda_rc(e);
+}
+
+uint64_t cg_growth_group_order(cg_growth_t h) { return h ? h->order : 0; }
+
+int cg_growth_get_stats(cg_growth_t h, cg_growth_stats* out) {
+    if (!h || !out) return CG_EINVAL;
+    *out = h->stats;
+    return CG_OK;
+}
+
+int cg_growth_destroy(cg_growth_t h) {
+    if (!h) return CG_OK;
+    if (h->device >= 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur == h->device) {
+            h->release(nullptr);
+            cudaStreamSynchronize(nullptr);
+            if (h->ev0) cudaEventDestroy(h->ev0);
+            if (h->ev1) cudaEventDestroy(h->ev1);
+        }
+    }
+    delete h;
+    return CG_OK;
+}
+
+const char* cg_strerror(int code) {
+    switch (code) {
+        case CG_OK: return "ok: the growth ended (next layer empty)";
+        case CG_TRUNC_RADIUS: return "stopped at max_radius (reported layers are exact)";
+        case CG_TRUNC_MEMCAP: return "stopped: the next layer did not fit in mem_cap (reported layers are exact)";
+        case CG_TRUNC_ABOVE: return "stopped after the first layer above stop_above (reported layers are exact)";
+        case CG_EINVAL: return "invalid argument";
+        case CG_ENOTCLOSED: return "generating set is not closed under inverse";
+        case CG_ENOMEM: return "device memory allocation failed";
+        case CG_ECUDA: return "CUDA runtime error";
+        case CG_EDEVICE: return "kernel reported an internal error";
+        case CG_ETIMEOUT: return "a bounded device-side wait timed out";
+        default: return "unknown code";
+    }
+}
+
+// ---- step-level kernels ---------------------------------------------------------------------
+
+int cg_expand(int n, int k, const uint8_t* gens, const uint64_t* frontier, uint64_t F,
+              uint64_t* out, void* cuda_stream) {
+    int rc = validate(n, k, gens);
+    if (rc) return rc;
+    if (F > 0 && (!frontier || !out)) return CG_EINVAL;
+    if (F == 0) return CG_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::vector<GenSM> g;
+    for (int j = 0; j < k; ++j) g.push_back(make_gensm(gens + (size_t)j * n, n));
+    GenSM* d = (GenSM*)dev_alloc(sizeof(GenSM) * k, st);
+    if (!d) return CG_ENOMEM;
+    cudaError_t e = cudaMemcpyAsync(d, g.data(), sizeof(GenSM) * k, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cg::launch_expand(d, k, frontier, F, out, 152 * 8, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // g is host stack memory
+    dev_free(d, st);
+    return cuda_rc(e);
+}
+
+int cg_hash_clear(uint64_t* table, uint64_t slots, void* cuda_stream) {
+    if (!table && slots) return CG_EINVAL;
+    return cuda_rc(cudaMemsetAsync(table, 0xFF, slots * 8, (cudaStream_t)cuda_stream));
+}
+
+int cg_hash_insert(uint64_t* table, uint64_t slots, const uint64_t* keys, uint64_t N,
+                   uint64_t* new_out, uint64_t* new_count, void* cuda_stream) {
+    if (!table || !new_count || slots == 0 || (slots & (slots - 1))) return CG_EINVAL;
+    if (N > 0 && (!keys || !new_out)) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int* fail = (int*)dev_alloc(sizeof(int), st);
+    if (!fail) return CG_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(fail, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(new_count, 0, sizeof(uint64_t), st);
+    if (e == cudaSuccess && N > 0)
+        e = cg::launch_hash_insert(table, slots - 1, keys, N, new_out,
+                                   (unsigned long long*)new_count, fail, 152 * 8, st);
+    dev_free(fail, st);
+    return cuda_rc(e);
+}
+
+}  // extern "C"
+
+// ---- batch of independent jobs ----------------------------------------------------------------
+struct cg_batch {
+    struct Job {
+        int n = 0, k = 0, max_radius = -1;
+        std::vector<GenSM> gsm;
+        uint64_t order = 1;
+        uint64_t cap = 1;          // states the job may store
+    };
+    std::vector<Job> jobs;
+    uint64_t mem_cap = kDefaultMemCap;
+};
+
+namespace {
+
+struct BatchBuffers {
+    void* block = nullptr;
+};
+
+// Run jobs [first, last) of b in one persistent launch.  Writes layer sizes and statuses.
+int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t* layer_out,
+             int cap, int* nl_out, int* status_out, int grid) {
+    const int nj = (int)ids.size();
+    if (nj == 0) return CG_OK;
+    // layout: gens | jobs | ubeg | layers | keys | tables   (each 256-byte aligned)
+    auto al = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+    uint64_t ngens = 0, nkeys = 0, nslots = 0;
+    std::vector<uint64_t> goff(nj), koff(nj), toff(nj), slots(nj);
+    for (int i = 0; i < nj; ++i) {
+        const auto& J = b->jobs[ids[i]];
+        goff[i] = ngens; ngens += J.gsm.size();
+        koff[i] = nkeys; nkeys += J.cap;
+        slots[i] = table_slots_for(J.cap);
+        toff[i] = nslots; nslots += slots[i];
+    }
+    const int lcap = cap + 1;
+    const uint64_t o_gens = 0;
+    const uint64_t o_jobs = al(o_gens + ngens * sizeof(GenSM));
+    const uint64_t o_ubeg = al(o_jobs + nj * sizeof(JobDev));
+    const uint64_t o_ctl = al(o_ubeg + (nj + 1) * 8);
+    const uint64_t o_lay = al(o_ctl + sizeof(Ctl));
+    const uint64_t o_keys = al(o_lay + (uint64_t)nj * lcap * 8);
+    const uint64_t o_tab = al(o_keys + nkeys * 8);
+    const uint64_t total = al(o_tab + nslots * 8);
+    char* base = (char*)dev_alloc(total, st);
+    if (!base) return CG_ENOMEM;
+    int rc = CG_OK;
+    std::vector<GenSM> hg;
+    hg.reserve(ngens);
+    std::vector<JobDev> hj(nj);
+    for (int i = 0; i < nj; ++i) {
+        const auto& J = b->jobs[ids[i]];
+        hg.insert(hg.end(), J.gsm.begin(), J.gsm.end());
+        JobDev& D = hj[i];
+        std::memset(&D, 0, sizeof(D));
+        D.keys = (uint64_t*)(base + o_keys) + koff[i];
+        D.keys_cap = J.cap;
+        D.table = (uint64_t*)(base + o_tab) + toff[i];
+        D.table_mask = slots[i] - 1;
+        D.gens = (const GenSM*)(base + o_gens) + goff[i];
+        D.layer_sizes = (uint64_t*)(base + o_lay) + (uint64_t)i * lcap;
+        D.k = J.k;
+        D.n = J.n;
+        D.layers_cap = lcap;
+        D.max_radius = J.max_radius;
+    }
+    JobDev* d_jobs = (JobDev*)(base + o_jobs);
+    unsigned long long* d_ubeg = (unsigned long long*)(base + o_ubeg);
+    Ctl* d_ctl = (Ctl*)(base + o_ctl);
+    cudaError_t e = cudaSuccess;
+    if (ngens) e = cudaMemcpyAsync(base + o_gens, hg.data(), ngens * sizeof(GenSM), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, hj.data(), nj * sizeof(JobDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tab, 0xFF, nslots * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
+    if (e == cudaSuccess)
+        e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, grid, lcap + 1, kTimeoutNs, st);
+    Ctl ctl;
+    std::memset(&ctl, 0, sizeof(ctl));
+    std::vector<uint64_t> lay((uint64_t)nj * lcap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hj.data(), d_jobs, nj * sizeof(JobDev), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lay.data(), base + o_lay, lay.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_rc(e);
+    else if (ctl.err) rc = ctl.err;
+    if (rc == CG_OK) {
+        for (int i = 0; i < nj; ++i) {
+            const int j = ids[i];
+            const int layers = hj[i].radius + 1;
+            int st_rc = status_to_rc(hj[i].status);
+            if (layers > cap) { st_rc = CG_EINVAL; rc = CG_EINVAL; }
+            nl_out[j] = layers;
+            for (int r = 0; r < layers && r < cap; ++r) layer_out[(uint64_t)j * cap + r] = lay[(uint64_t)i * lcap + r];
+            if (status_out) status_out[j] = st_rc;
+            if (st_rc < 0 && rc == CG_OK) rc = st_rc;
+        }
+    }
+    dev_free(base, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_batch_create(int njobs, const int* n, const int* k, const uint8_t* gens,
+                    const uint64_t* gens_offset, const int* inverse_closed,
+                    const int* max_radius, uint64_t mem_cap, cg_batch_t* out) {
+    if (!out || njobs < 0 || (njobs > 0 && (!n || !k || !gens || !gens_offset))) return CG_EINVAL;
+    *out = nullptr;
+    cg_batch* b = new (std::nothrow) cg_batch();
+    if (!b) return CG_ENOMEM;
+    b->mem_cap = mem_cap ? mem_cap : kDefaultMemCap;
+    b->jobs.resize(njobs);
+    for (int j = 0; j < njobs; ++j) {
+        const uint8_t* g = gens + gens_offset[j];
+        int rc = validate(n[j], k[j], g);
+        if (rc) { delete b; return rc; }
+        auto rows = clean_rows(n[j], k[j], g);
+        if (inverse_closed && inverse_closed[j] && !closed_under_inverse(rows, n[j])) {
+            delete b;
+            return CG_ENOTCLOSED;
+        }
+        auto& J = b->jobs[j];
+        J.n = n[j];
+        J.k = (int)rows.size();
+        J.max_radius = (max_radius && max_radius[j] >= 0) ? max_radius[j] : -1;
+        for (auto& r : rows) J.gsm.push_back(make_gensm(r.data(), n[j]));
+        std::vector<uint8_t> flat;
+        for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
+        J.order = rows.empty() ? 1 : cg::group_order(n[j], (int)rows.size(), flat.data());
+    }
+    *out = b;
+    return CG_OK;
+}
+
+int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int cap,
+                 int* num_layers_out, int* status_out) {
+    if (!b || !num_layers_out || cap < 1 || (!layer_sizes_out && !b->jobs.empty())) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_rc(e);
+    const int grid = grow_grid(dev);
+    if (grid <= 0) return CG_ECUDA;
+    const uint64_t budget = b->mem_cap;
+    const uint64_t per_job_max = max_cap_for_mem(budget / 2);
+    // Greedy waves in job order, each within the memory budget.
+    std::vector<int> wave;
+    uint64_t wave_bytes = 0;
+    int rc = CG_OK;
+    auto flush = [&]() {
+        int r = run_wave(b, wave, st, layer_sizes_out, cap, num_layers_out, status_out, grid);
+        if (r != CG_OK && rc == CG_OK) rc = r;
+        wave.clear();
+        wave_bytes = 0;
+    };
+    for (int j = 0; j < (int)b->jobs.size(); ++j) {
+        auto& J = b->jobs[j];
+        if (J.k == 0 || J.max_radius == 0) {
+            num_layers_out[j] = 1;
+            layer_sizes_out[(uint64_t)j * cap] = 1;
+            if (status_out) status_out[j] = J.k == 0 ? CG_OK : CG_TRUNC_RADIUS;
+            continue;
+        }
+        J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
+        const uint64_t need = bytes_for(J.cap) + sizeof(GenSM) * J.gsm.size() + sizeof(JobDev) +
+                              (uint64_t)(cap + 1) * 8 + 1024;
+        if (!wave.empty() && wave_bytes + need > budget) flush();
+        wave.push_back(j);
+        wave_bytes += need;
+    }
+    if (!wave.empty()) flush();
+    return rc;
+}
+
+int cg_batch_destroy(cg_batch_t b) {
+    delete b;
+    return CG_OK;
+}
+
+}  // extern "C"

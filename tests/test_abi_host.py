@@ -1,0 +1,113 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol include/*.h declares,
+and its host-side logic (validation, inverse-closure check, group order) is right.  No call
+here touches a GPU."""
+
+import ctypes
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_19162_gb300 import build
+    build()
+    from paper_2509_19162_gb300 import _cg
+    return _cg
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(cg_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "cg_growth_create" in names and "cg_growth_run" in names
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in sorted(names):
+        assert hasattr(so, name), f"{name} declared in include/ but not exported"
+    # and the binding wraps every one of them under the same name
+    for name in names:
+        assert hasattr(lib, name), f"binding lacks {name}"
+
+
+def test_strerror_names_every_code(lib):
+    for code in (0, 1, 2, 3, -1, -2, -3, -4, -5, -6):
+        assert lib.strerror(code) != "unknown code"
+
+
+def _create(lib, n, gens, inv=0, maxr=-1):
+    g = np.ascontiguousarray(np.asarray(gens, dtype=np.uint8))
+    h = ctypes.c_void_p()
+    rc = lib.cg_growth_create(n, len(gens), g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                              inv, maxr, 0, ctypes.byref(h))
+    return rc, h
+
+
+def test_create_validation(lib):
+    assert _create(lib, 3, [[0, 0, 1]])[0] == lib.CG_EINVAL          # not a permutation
+    assert _create(lib, 17, [list(range(17))])[0] == lib.CG_EINVAL   # n > 16
+    assert _create(lib, 0, [[]])[0] == lib.CG_EINVAL
+    assert _create(lib, 5, w.lx(5), inv=1)[0] == lib.CG_ENOTCLOSED
+    rc, h = _create(lib, 5, w.lrx(5), inv=1)
+    assert rc == 0 and h.value
+    assert lib.cg_growth_set_option(h, 99, 0) == lib.CG_EINVAL
+    assert lib.cg_growth_set_option(h, lib.CG_OPT_STRATEGY, 7) == lib.CG_EINVAL
+    assert lib.cg_growth_destroy(h) == 0
+    assert lib.cg_growth_destroy(None) == 0
+    # sort strategy needs an inverse-closed set
+    rc, h = _create(lib, 5, w.lx(5), inv=0)
+    assert lib.cg_growth_set_option(h, lib.CG_OPT_STRATEGY, lib.CG_STRATEGY_SORT) == lib.CG_EINVAL
+    lib.cg_growth_destroy(h)
+
+
+def test_group_order_closed_forms(lib):
+    from paper_2509_19162_gb300 import Growth
+    for n in range(2, 17):
+        assert Growth(n, w.coxeter(n)).order == math.factorial(n)
+        if n >= 3:
+            assert Growth(n, w.three_cycles(n) if n <= 9 else w.consecutive_3cycles_inv(n)).order \
+                == math.factorial(n) // 2
+    assert Growth(16, w.all_transpositions(16)).order == math.factorial(16)
+    # identity / duplicate rows are ignored
+    g = w.coxeter(6)
+    assert Growth(6, g + g + [list(range(6))]).order == 720
+    assert Growth(4, [[0, 1, 2, 3]]).order == 1
+
+
+def test_group_order_matches_sympy(lib):
+    sc = pytest.importorskip("sympy.combinatorics")
+    from paper_2509_19162_gb300 import Growth
+    rng = np.random.default_rng(99)
+    for _ in range(60):
+        n = int(rng.integers(2, 17))
+        gens = w.random_perms(rng, n, int(rng.integers(1, 4)))
+        if rng.integers(0, 2):
+            # a subgroup: generators that fix the last points or move blocks
+            m = int(rng.integers(1, n + 1))
+            gens = [g[:m] + list(range(m, n)) if sorted(g[:m]) == list(range(m)) else g for g in gens]
+        want = sc.PermutationGroup([sc.Permutation(g) for g in gens]).order()
+        assert Growth(n, gens).order == want
+
+
+def test_batch_create_validation(lib):
+    from paper_2509_19162_gb300 import Batch
+    jobs = [(n, w.coxeter(n), True, -1) for n in (3, 4, 5)]
+    b = Batch(jobs)
+    b.close()
+    with pytest.raises(RuntimeError):
+        Batch([(5, w.lx(5), True, -1)])
