@@ -54,6 +54,12 @@ extern "C" {
 #define CG_OPT_STRATEGY     1  /* one of CG_STRATEGY_*                                        */
 #define CG_OPT_STOP_ABOVE   2  /* > 0: stop after the first layer with more states than this */
 #define CG_OPT_KEEP_LAST    3  /* 1: keep the last layer's states for cg_growth_last_layer    */
+#define CG_OPT_GRID         4  /* > 0: blocks of the persistent launch (capped at co-residency);
+                                  0: library chooses                                          */
+#define CG_OPT_ILP          5  /* 1..4: generators whose probe sequences one thread advances
+                                  together, probing one slot per step; 9..12: the same with
+                                  ILP = value - 8, probing a whole 32-byte sector per step;
+                                  0: library chooses                                          */
 
 /* ---- device memory ------------------------------------------------------------------ */
 /*

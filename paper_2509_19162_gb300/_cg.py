@@ -30,6 +30,8 @@ CG_STRATEGY_SORT = 2
 CG_OPT_STRATEGY = 1
 CG_OPT_STOP_ABOVE = 2
 CG_OPT_KEEP_LAST = 3
+CG_OPT_GRID = 4
+CG_OPT_ILP = 5
 
 # Every symbol include/cg_growth.h declares: name -> (restype, argtypes)
 _u8p = ctypes.POINTER(ctypes.c_uint8)

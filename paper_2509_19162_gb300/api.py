@@ -121,6 +121,14 @@ class Growth:
         _cg.check(rc, "cg_growth_run")
         return GrowthResult([int(x) for x in self._out[:nl.value]], rc)
 
+    def set_grid(self, blocks: int) -> None:
+        """Blocks of the persistent launch (0 = library default)."""
+        _cg.check(_cg.cg_growth_set_option(self._h, _cg.CG_OPT_GRID, int(blocks)), "set_grid")
+
+    def set_ilp(self, ilp: int) -> None:
+        """Generators probed together per thread (1..4; 0 = library default)."""
+        _cg.check(_cg.cg_growth_set_option(self._h, _cg.CG_OPT_ILP, int(ilp)), "set_ilp")
+
     def stats(self) -> dict:
         st = _cg.cg_growth_stats()
         _cg.check(_cg.cg_growth_get_stats(self._h, ctypes.byref(st)), "cg_growth_get_stats")

@@ -85,6 +85,121 @@ __device__ __forceinline__ int table_insert(uint64_t* table, uint64_t mask, uint
     return -1;
 }
 
+// Two 16-byte loads served by L2 (cache-global, never a stale L1 line) covering one aligned
+// 32-byte sector = 4 table slots.  Weak loads are enough: a slot, once written, never changes,
+// and a stale "empty" is caught by the CAS that follows.
+__device__ __forceinline__ void ld_sector(const uint64_t* p, uint64_t (&v)[4]) {
+    const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+    const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// G independent insert-if-absent sequences (linear probing) advanced together, so that one
+// thread keeps G sector loads (and CASes) in flight.  Each step reads the aligned 4-slot
+// sector holding the current slot and scans it from that slot on: a match ends the sequence
+// (already present); the first empty slot gets a CAS; a full sector moves on to the next.
+// res[i] as for table_insert; entries i >= nvalid are left at 0.
+template <int G>
+__device__ __forceinline__ void table_insert_multi_sector(uint64_t* table, uint64_t mask,
+                                                          const uint64_t (&key)[G], int (&res)[G],
+                                                          int nvalid, uint64_t max_steps) {
+    uint64_t h[G];
+    unsigned pend = 0;   // bit i: sequence i still probing
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        res[i] = 0;
+        if (i < nvalid) pend |= 1u << i;
+        h[i] = mix64(key[i]) & mask;
+    }
+    for (uint64_t step = 0; pend && step < max_steps; ++step) {
+        uint64_t v[G][4];
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            if (pend >> i & 1u) ld_sector(table + (h[i] & ~3ull), v[i]);
+        unsigned cas = 0;
+        uint64_t old[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            if (!(pend >> i & 1u)) continue;
+            const unsigned off = (unsigned)(h[i] & 3u);
+            int hit = -1, empty = -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((unsigned)q >= off && hit < 0 && empty < 0) {
+                    if (v[i][q] == key[i]) hit = q;
+                    else if (v[i][q] == kEmpty) empty = q;
+                }
+            }
+            if (hit >= 0) {
+                pend &= ~(1u << i);
+            } else if (empty >= 0) {
+                h[i] = (h[i] & ~3ull) | (unsigned)empty;
+                cas |= 1u << i;
+                old[i] = atomicCAS(reinterpret_cast<unsigned long long*>(table + h[i]),
+                                   (unsigned long long)kEmpty, (unsigned long long)key[i]);
+            } else {
+                h[i] = ((h[i] | 3ull) + 1) & mask;   // next sector
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            if (cas >> i & 1u) {
+                if (old[i] == kEmpty) { res[i] = 1; pend &= ~(1u << i); }
+                else if (old[i] == key[i]) { pend &= ~(1u << i); }
+                else h[i] = (h[i] + 1) & mask;       // lost the slot: continue after it
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+        if (pend >> i & 1u) res[i] = -1;
+}
+
+// As table_insert_multi_sector, but each step reads the single current slot (8 bytes).
+template <int G>
+__device__ __forceinline__ void table_insert_multi_slot(uint64_t* table, uint64_t mask,
+                                                        const uint64_t (&key)[G], int (&res)[G],
+                                                        int nvalid, uint64_t max_steps) {
+    uint64_t h[G];
+    unsigned pend = 0;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        res[i] = 0;
+        if (i < nvalid) pend |= 1u << i;
+        h[i] = mix64(key[i]) & mask;
+    }
+    for (uint64_t step = 0; pend && step < max_steps; ++step) {
+        uint64_t v[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            if (pend >> i & 1u) v[i] = __ldcg(table + h[i]);
+        unsigned cas = 0;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            if (pend >> i & 1u) {
+                if (v[i] == key[i]) {
+                    pend &= ~(1u << i);
+                } else if (v[i] == kEmpty) {
+                    cas |= 1u << i;
+                    v[i] = atomicCAS(reinterpret_cast<unsigned long long*>(table + h[i]),
+                                     (unsigned long long)kEmpty, (unsigned long long)key[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            if (cas >> i & 1u) {
+                if (v[i] == kEmpty) { res[i] = 1; pend &= ~(1u << i); }
+                else if (v[i] == key[i]) { pend &= ~(1u << i); }
+            }
+            if (pend >> i & 1u) h[i] = (h[i] + 1) & mask;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+        if (pend >> i & 1u) res[i] = -1;
+}
+
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  Waits are bounded by
 // `timeout_ns` of wall time; on timeout the error word is set to CG_ETIMEOUT and false is
 // returned, as it is when another block has already set the error word.  Callers return
@@ -104,14 +219,17 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, uint64_t timeout_ns) {
             atomicAdd(&ctl->bar_gen, 1u);
         } else {
             const uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
             while (*vgen == gen) {
-                if (*(volatile int*)&ctl->err != 0) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > timeout_ns) {
-                    atomicCAS(&ctl->err, 0, CG_ETIMEOUT);
-                    ok = 0;
-                    break;
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int*)&ctl->err != 0) { ok = 0; break; }
+                    if (globaltimer_ns() - t0 > timeout_ns) {
+                        atomicCAS(&ctl->err, 0, CG_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(100);
+                __nanosleep(spins < 64 ? 32 : 256);
             }
         }
         __threadfence();

@@ -31,7 +31,9 @@ enum JobStatus : int {
 };
 
 // One growth job of the hash strategy as the persistent kernel sees it.
-struct JobDev {
+// 256 bytes: the read-only fields fill the first 128-byte line, the fields updated during a
+// run (read by every SM, bumped with atomics) live alone in the second.
+struct alignas(128) JobDev {
     // static, written by the host
     uint64_t* keys;            // all layers back to back; layer r = keys[off_r, off_{r+1})
     uint64_t keys_cap;
@@ -45,7 +47,7 @@ struct JobDev {
     int layers_cap;
     int max_radius;            // < 0: unlimited
     // dynamic, updated between rounds by block 0
-    unsigned long long lo;     // frontier = keys[lo, hi)
+    alignas(128) unsigned long long lo;     // frontier = keys[lo, hi)
     unsigned long long hi;
     unsigned long long tail;   // append cursor (atomic during a round)
     int radius;                // radius of the frontier layer
@@ -55,9 +57,13 @@ struct JobDev {
 };
 
 // Control block of the persistent kernel (device memory, zero-initialised by the host).
-struct Ctl {
+// The barrier's arrival counter and the generation word that waiting blocks poll sit in
+// different 128-byte lines, so polling does not queue behind arrivals at one L2 slice.
+struct alignas(128) Ctl {
     unsigned int bar_count;
+    unsigned int pad0[31];
     unsigned int bar_gen;
+    unsigned int pad1[31];
     int err;                        // 0, or a CG_E* code set by a kernel
     int rounds;                     // rounds completed
     unsigned long long total_units; // warp work units of the current round

@@ -10,13 +10,14 @@ namespace cg {
 
 // hash strategy (hash_path.cu)
 int hash_grow_block();
-int hash_grow_max_grid(int device);
+int hash_grow_max_grid(int device, int ilp);
 cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              cudaStream_t st);
 cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                                 cudaStream_t st);
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
-                             int grid, int max_rounds, uint64_t timeout_ns, cudaStream_t st);
+                             int grid, int max_rounds, uint64_t timeout_ns, int ilp,
+                             cudaStream_t st);
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,
                                  uint64_t mask, int* d_err, int grid, cudaStream_t st);
 cudaError_t launch_expand(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,

@@ -22,7 +22,7 @@ namespace cg {
 namespace {
 
 constexpr int kGrowBlock = 256;
-constexpr uint64_t kMaxProbe = 1ull << 16;
+constexpr uint64_t kMaxProbe = 1ull << 16;   // probe steps (sectors) before giving up
 
 // Largest j with ubeg[j] <= u (ubeg ascending, ubeg[0] = 0).
 __device__ __forceinline__ int find_job(const unsigned long long* ubeg, int njobs,
@@ -68,8 +68,7 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
                         else if (r + 1 >= J.layers_cap) J.status = kTruncRadius;
                     }
                 }
-                if (J.status == kRunning)
-                    units = (unsigned long long)J.k * ((J.hi - J.lo + 31) >> 5);
+                if (J.status == kRunning) units = (J.hi - J.lo + 31) >> 5;
             }
         }
         // block-wide exclusive scan of units
@@ -104,49 +103,118 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
     }
 }
 
-__global__ void __launch_bounds__(kGrowBlock)
+// Per-warp staging of newly found states in shared memory: a warp appends its winners to
+// its own buffer and reserves room in the job's key array with one atomic per flush, which
+// turns a per-unit atomic on one global counter into one per ~kStage/32 units and writes the
+// keys out coalesced.
+constexpr int kStage = 256;
+
+__device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, int lane) {
+    if (cnt == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&J->tail, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    uint64_t* keys = J->keys;
+    const unsigned long long cap = J->keys_cap;
+    bool over = false;
+    for (int i = lane; i < cnt; i += 32) {
+        const unsigned long long pos = base + i;
+        if (pos < cap) keys[pos] = buf[i];
+        else over = true;
+    }
+    if (__any_sync(0xffffffffu, over) && lane == 0) atomicExch(&J->overflow, 1);
+    cnt = 0;
+    __syncwarp();
+}
+
+// One unit = 32 frontier states (one per lane) of job J, every generator applied to each:
+// expand, insert-if-absent into the visited table, stage the winners.  kProbeILP generators
+// are handled together (that many independent probe sequences in flight per thread).
+template <int kProbeILP, bool kSector>
+__device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsigned long long hi,
+                                        uint64_t* buf, int& cnt, int lane, bool& overflow_seen) {
+    const bool active = idx < hi;
+    const uint64_t s = active ? __ldcg(J->keys + idx) : 0;
+    const int k = J->k;
+    const GenSM* gens = J->gens;
+    for (int g0 = 0; g0 < k; g0 += kProbeILP) {
+        const int ng = min(kProbeILP, k - g0);
+        uint64_t t[kProbeILP];
+        int res[kProbeILP];
+#pragma unroll
+        for (int i = 0; i < kProbeILP; ++i) t[i] = (i < ng) ? apply_gen(gens[g0 + i], s) : 0;
+        if (kSector)
+            table_insert_multi_sector<kProbeILP>(J->table, J->table_mask, t, res, active ? ng : 0,
+                                                 kMaxProbe);
+        else
+            table_insert_multi_slot<kProbeILP>(J->table, J->table_mask, t, res, active ? ng : 0,
+                                               kMaxProbe);
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < kProbeILP; ++i) bad |= (res[i] < 0);
+        if (__any_sync(0xffffffffu, bad)) {
+            overflow_seen = true;
+            if (lane == 0) atomicExch(&J->overflow, 1);
+        }
+#pragma unroll
+        for (int i = 0; i < kProbeILP; ++i) {
+            const unsigned fresh = __ballot_sync(0xffffffffu, res[i] == 1);
+            if (res[i] == 1) buf[cnt + __popc(fresh & lanemask_lt())] = t[i];
+            cnt += __popc(fresh);
+            __syncwarp();
+            if (cnt > kStage - 32) stage_flush(buf, cnt, J, lane);
+        }
+    }
+}
+
+template <int kProbeILP, bool kSector>
+__global__ void __launch_bounds__(kGrowBlock, (kSector && kProbeILP >= 3) ? 2 : 3)
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
                  uint64_t timeout_ns) {
+    __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
     const int lane = threadIdx.x & 31;
+    uint64_t* buf = s_stage[threadIdx.x >> 5];
     const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
 
     for (int round = 0; round < max_rounds; ++round) {
         const unsigned long long total = ld_relaxed_ull(&ctl->total_units);
         if (total == 0) break;
-
-        for (unsigned long long u = warp0; u < total; u += nwarps) {
-            const int j = njobs == 1 ? 0 : find_job(ubeg, njobs, u);
-            JobDev* J = jobs + j;
-            if (ld_relaxed_int(&J->overflow)) continue;
+        int cnt = 0;
+        bool overflow_seen = false;
+        if (njobs == 1) {
+            // One job: its frontier is fixed for the round.
+            JobDev* J = jobs;
             const unsigned long long lo = ld_relaxed_ull(&J->lo);
             const unsigned long long hi = ld_relaxed_ull(&J->hi);
-            const unsigned long long nblk = (hi - lo + 31) >> 5;
-            const unsigned long long local = u - ld_relaxed_ull(ubeg + j);
-            const unsigned g = (unsigned)(local / nblk);
-            const unsigned long long idx = lo + ((local - g * nblk) << 5) + lane;
-            uint64_t* keys = J->keys;
-            int ins = 0;
-            uint64_t t = 0;
-            if (idx < hi) {
-                const uint64_t s = __ldcg(keys + idx);
-                t = apply_gen(J->gens[g], s);
-                ins = table_insert(J->table, J->table_mask, t, kMaxProbe);
+            unsigned iter = 0;
+            for (unsigned long long b = warp0; b < total; b += nwarps) {
+                do_unit<kProbeILP, kSector>(J, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen);
+                // Stop early once any warp found the job's buffers full (the layer will be
+                // redone after the host grows them).
+                if ((++iter & 15u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
+                    overflow_seen = true;
+                if (overflow_seen) break;
             }
-            const unsigned fresh = __ballot_sync(0xffffffffu, ins == 1);
-            if (__any_sync(0xffffffffu, ins < 0)) {
-                if (lane == 0) atomicExch(&J->overflow, 1);
-            }
-            if (fresh) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&J->tail, (unsigned long long)__popc(fresh));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (ins == 1) {
-                    const unsigned long long pos = base + __popc(fresh & lanemask_lt());
-                    if (pos < J->keys_cap) keys[pos] = t;
-                    else atomicExch(&J->overflow, 1);
+            stage_flush(buf, cnt, J, lane);
+        } else {
+            int cur = -1;
+            JobDev* J = nullptr;
+            unsigned long long lo = 0, hi = 0, u0 = 0;
+            for (unsigned long long u = warp0; u < total; u += nwarps) {
+                const int j = find_job(ubeg, njobs, u);
+                if (j != cur) {
+                    if (J) stage_flush(buf, cnt, J, lane);
+                    cur = j;
+                    J = jobs + j;
+                    lo = ld_relaxed_ull(&J->lo);
+                    hi = ld_relaxed_ull(&J->hi);
+                    u0 = ld_relaxed_ull(ubeg + j);
                 }
+                if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
+                do_unit<kProbeILP, kSector>(J, lo + ((u - u0) << 5) + lane, hi, buf, cnt, lane, overflow_seen);
             }
+            if (J) stage_flush(buf, cnt, J, lane);
         }
         if (!grid_barrier(ctl, timeout_ns)) return;
         if (blockIdx.x == 0) close_round(jobs, njobs, ubeg, ctl);
@@ -174,14 +242,13 @@ __global__ void init_jobs_kernel(JobDev* jobs, int njobs) {
 }
 
 // Work layout of the first round (after init, or after the host resized a job's buffers):
-// k warp units per 32 frontier states of every running job.
+// one warp unit per 32 frontier states of every running job.
 __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     unsigned long long acc = 0;
     for (int j = 0; j < njobs; ++j) {
         ubeg[j] = acc;
-        if (jobs[j].status == kRunning)
-            acc += (unsigned long long)jobs[j].k * ((jobs[j].hi - jobs[j].lo + 31) >> 5);
+        if (jobs[j].status == kRunning) acc += (jobs[j].hi - jobs[j].lo + 31) >> 5;
     }
     ubeg[njobs] = acc;
     ctl->total_units = acc;
@@ -246,10 +313,27 @@ __global__ void finish_insert_count_kernel(unsigned long long* count, const int*
 
 int hash_grow_block() { return kGrowBlock; }
 
-int hash_grow_max_grid(int device) {
+namespace {
+using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t);
+// Probe variants: `ilp` generators per thread (1..4); +8 selects whole-sector probing.
+GrowFn grow_fn(int variant) {
+    switch (variant) {
+        case 1: return hash_grow_kernel<1, false>;
+        case 2: return hash_grow_kernel<2, false>;
+        case 3: return hash_grow_kernel<3, false>;
+        case 4: return hash_grow_kernel<4, false>;
+        case 9: return hash_grow_kernel<1, true>;
+        case 10: return hash_grow_kernel<2, true>;
+        case 11: return hash_grow_kernel<3, true>;
+        default: return hash_grow_kernel<4, true>;
+    }
+}
+}  // namespace
+
+int hash_grow_max_grid(int device, int ilp) {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hash_grow_kernel, kGrowBlock, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grow_fn(ilp), kGrowBlock, 0) !=
         cudaSuccess)
         return 0;
     return sms * per_sm;
@@ -269,7 +353,7 @@ cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d
 }
 
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
-                             int grid, int max_rounds, uint64_t timeout_ns, cudaStream_t st) {
+                             int grid, int max_rounds, uint64_t timeout_ns, int ilp, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kGrowBlock);
@@ -280,7 +364,7 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, hash_grow_kernel, d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
+    return cudaLaunchKernelEx(&cfg, grow_fn(ilp), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
                               timeout_ns);
 }
 

@@ -27,7 +27,7 @@ namespace {
 
 constexpr uint64_t kDefaultMemCap = 160ull << 30;
 constexpr uint64_t kTimeoutNs = 30ull * 1000 * 1000 * 1000;  // per barrier wait
-constexpr double kMaxLoad = 0.75;                               // visited-table load limit
+constexpr double kMaxLoad = 0.5;                                // visited-table load limit
 constexpr uint64_t kExactAllocLimit = 24ull << 30;  // allocate |<S>| states up front below this
 
 // ---- allocator ------------------------------------------------------------------------
@@ -185,13 +185,18 @@ int status_to_rc(int status) {
     }
 }
 
-int device_grid_cache[64] = {};
+int device_grid_cache[64][16] = {};
 
-int grow_grid(int dev) {
-    if (dev < 0 || dev >= 64) return 0;
-    if (!device_grid_cache[dev]) device_grid_cache[dev] = cg::hash_grow_max_grid(dev);
-    return device_grid_cache[dev];
+// Blocks of the persistent kernel that fit co-resident on device `dev` (probe variant: ILP
+// 1..4, +8 for whole-sector probing).
+int grow_grid(int dev, int ilp) {
+    if (dev < 0 || dev >= 64 || ilp < 1 || ilp > 12) return 0;
+    if (!device_grid_cache[dev][ilp]) device_grid_cache[dev][ilp] = cg::hash_grow_max_grid(dev, ilp);
+    return device_grid_cache[dev][ilp];
 }
+
+// Generators probed together per thread: all of them when k <= 4, else 4.
+int default_ilp(int k) { return std::max(1, std::min(4, k)); }
 
 }  // namespace
 
@@ -206,6 +211,8 @@ struct cg_growth {
     int strategy = CG_STRATEGY_AUTO;
     uint64_t stop_above = 0;
     int keep_last = 0;
+    int grid_override = 0;
+    int ilp_override = 0;
     uint64_t order = 1;
     int device = -1;
     cudaStream_t alloc_stream = nullptr;
@@ -307,11 +314,13 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         rc = resize_state(h, std::max<uint64_t>(start, 1), 0, st);
         if (rc) return rc;
     }
-    const int grid_max = grow_grid(h->device);
+    const int ilp = h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k);
+    const int grid_max = grow_grid(h->device, ilp);
     if (grid_max <= 0) return CG_ECUDA;
     // Small groups finish faster with fewer blocks at each barrier.
-    const uint64_t want = (h->order * (uint64_t)std::max(1, h->k)) / (32 * 8 * 4) + 1;
-    const int grid = (int)std::min<uint64_t>((uint64_t)grid_max, std::max<uint64_t>(want, 1));
+    const uint64_t want = h->order / (32 * 8 * 2) + 1;
+    int grid = (int)std::min<uint64_t>((uint64_t)grid_max, std::max<uint64_t>(want, 1));
+    if (h->grid_override > 0) grid = std::min(grid_max, h->grid_override);
 
     cudaError_t e = cudaMemsetAsync(h->d_table, 0xFF, h->table_slots * 8, st);
     if (e != cudaSuccess) return cuda_rc(e);
@@ -332,7 +341,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     for (;;) {
         if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
         if ((e = cg::launch_hash_grow(h->d_job, 1, h->d_ubeg, h->d_ctl, grid, cg::kMaxLayers + 1,
-                                      kTimeoutNs, st)) != cudaSuccess)
+                                      kTimeoutNs, ilp, st)) != cudaSuccess)
             return cuda_rc(e);
         if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
         h->stats.launches += 1;
@@ -425,6 +434,14 @@ int cg_growth_set_option(cg_growth_t h, int option, int64_t value) {
             return CG_OK;
         case CG_OPT_KEEP_LAST:
             h->keep_last = value ? 1 : 0;
+            return CG_OK;
+        case CG_OPT_GRID:
+            if (value < 0 || value > (1 << 20)) return CG_EINVAL;
+            h->grid_override = (int)value;
+            return CG_OK;
+        case CG_OPT_ILP:
+            if (value < 0 || value > 12 || (value > 4 && value < 9)) return CG_EINVAL;
+            h->ilp_override = (int)value;
             return CG_OK;
         default:
             return CG_EINVAL;
@@ -575,7 +592,7 @@ struct BatchBuffers {
 
 // Run jobs [first, last) of b in one persistent launch.  Writes layer sizes and statuses.
 int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t* layer_out,
-             int cap, int* nl_out, int* status_out, int grid) {
+             int cap, int* nl_out, int* status_out, int grid, int ilp) {
     const int nj = (int)ids.size();
     if (nj == 0) return CG_OK;
     // layout: gens | jobs | ubeg | layers | keys | tables   (each 256-byte aligned)
@@ -630,7 +647,7 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
     if (e == cudaSuccess)
-        e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, grid, lcap + 1, kTimeoutNs, st);
+        e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, grid, lcap + 1, kTimeoutNs, ilp, st);
     Ctl ctl;
     std::memset(&ctl, 0, sizeof(ctl));
     std::vector<uint64_t> lay((uint64_t)nj * lcap);
@@ -699,7 +716,10 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_rc(e);
-    const int grid = grow_grid(dev);
+    int maxk = 1;
+    for (auto& J : b->jobs) maxk = std::max(maxk, J.k);
+    const int ilp = default_ilp(maxk);
+    const int grid = grow_grid(dev, ilp);
     if (grid <= 0) return CG_ECUDA;
     const uint64_t budget = b->mem_cap;
     const uint64_t per_job_max = max_cap_for_mem(budget / 2);
@@ -708,7 +728,7 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     uint64_t wave_bytes = 0;
     int rc = CG_OK;
     auto flush = [&]() {
-        int r = run_wave(b, wave, st, layer_sizes_out, cap, num_layers_out, status_out, grid);
+        int r = run_wave(b, wave, st, layer_sizes_out, cap, num_layers_out, status_out, grid, ilp);
         if (r != CG_OK && rc == CG_OK) rc = r;
         wave.clear();
         wave_bytes = 0;

@@ -11,6 +11,7 @@ from .families import (  # noqa: F401
     all_transpositions,
     consecutive_3cycles_inv,
     coxeter,
+    cycle,
     cycles_01i_inv,
     cyclic_coxeter,
     from_cycles,
