@@ -43,6 +43,8 @@ extern "C" {
 #define CG_ECUDA           -4  /* a CUDA runtime call failed                                 */
 #define CG_EDEVICE         -5  /* a kernel reported an internal error (error word set)       */
 #define CG_ETIMEOUT        -6  /* a bounded device-side wait ran out; the kernel returned    */
+#define CG_ETOOBIG         -7  /* the problem exceeds the fixed scratch of
+                                  cg_growth_run_noalloc (CG_NOALLOC_MAX_*)                    */
 
 /* ---- strategies (cg_growth_set_option(h, CG_OPT_STRATEGY, ...)) --------------------- */
 #define CG_STRATEGY_AUTO    0  /* library chooses                                             */
@@ -172,6 +174,37 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
 
 /* Release the batch and its device buffers.  NULL is accepted. */
 int cg_batch_destroy(cg_batch_t b);
+
+/* ---- growth without allocation ------------------------------------------------------- */
+/*
+ * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory when they need a growth -- code inside a memory-capped sandbox or a
+ * pre-reserved pool, a latency-critical process that forbids cudaMalloc (which can synchronise
+ * the device) after start-up, or a plugin whose host application owns every allocation.
+ *
+ * cg_growth_run_noalloc computes the same growth as cg_growth_create + cg_growth_run +
+ * cg_growth_destroy (hash strategy, same kernels) but calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its buffers live in one fixed device array inside the library
+ * (about 24.2 MiB: CG_NOALLOC_MAX_STATES states plus a visited table of twice that many
+ * slots), which every GPU that loads the library holds until the process exits.
+ *   n, k, gens, inverse_closed, max_radius   as for cg_growth_create (gens: host pointer).
+ *   cuda_stream                              stream to run on; synchronised before returning.
+ *   layer_sizes_out, cap, num_layers_out     as for cg_growth_run (host pointers).
+ * Limits: at most CG_NOALLOC_MAX_GENS generators, and the growth may visit at most
+ * CG_NOALLOC_MAX_STATES states (for a complete growth: the group order); beyond either the
+ * call returns CG_ETOOBIG and reports nothing.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture on that device.
+ * All calls share the array, which keeps the last call's contents; each call clears what
+ * must start empty.  Calls are serialised on the host and wait for their stream, so they do
+ * not overlap; anything else that touched the array while a call runs would race with it.
+ * Returns the same codes as cg_growth_run, plus CG_ETOOBIG.
+ */
+#define CG_NOALLOC_MAX_STATES (1u << 20)
+#define CG_NOALLOC_MAX_GENS   256
+int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
+                          void* cuda_stream, uint64_t* layer_sizes_out, int cap,
+                          int* num_layers_out);
 
 /* ---- step-level kernels (device pointers, asynchronous on the given stream) ----------- */
 

@@ -22,6 +22,7 @@ CG_ENOMEM = -3
 CG_ECUDA = -4
 CG_EDEVICE = -5
 CG_ETIMEOUT = -6
+CG_ETOOBIG = -7
 
 CG_STRATEGY_AUTO = 0
 CG_STRATEGY_HASH = 1
@@ -62,6 +63,8 @@ SIGNATURES = {
                                        ctypes.POINTER(_vp)]),
     "cg_batch_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip, _ip]),
     "cg_batch_destroy": (ctypes.c_int, [_vp]),
+    "cg_growth_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int,
+                                             _vp, _u64p, ctypes.c_int, _ip]),
     "cg_expand": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_hash_insert": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
     "cg_hash_clear": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp]),
@@ -117,6 +120,7 @@ cg_strerror = _export("cg_strerror")
 cg_batch_create = _export("cg_batch_create")
 cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")
+cg_growth_run_noalloc = _export("cg_growth_run_noalloc")
 cg_expand = _export("cg_expand")
 cg_hash_insert = _export("cg_hash_insert")
 cg_hash_clear = _export("cg_hash_clear")

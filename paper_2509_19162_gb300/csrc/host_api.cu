@@ -525,6 +525,7 @@ const char* cg_strerror(int code) {
         case CG_ECUDA: return "CUDA runtime error";
         case CG_EDEVICE: return "kernel reported an internal error";
         case CG_ETIMEOUT: return "a bounded device-side wait timed out";
+        case CG_ETOOBIG: return "problem exceeds the fixed scratch of cg_growth_run_noalloc";
         default: return "unknown code";
     }
 }
