@@ -68,6 +68,10 @@ SIGNATURES = {
     "cg_expand": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_hash_insert": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
     "cg_hash_clear": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp]),
+    "cg_sort_unique_scratch_bytes": (ctypes.c_size_t, [ctypes.c_uint64]),
+    "cg_sort_unique": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "cg_set_difference": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, ctypes.c_uint64,
+                                         _vp, _vp, _vp, ctypes.c_size_t, _vp]),
 }
 
 
@@ -124,3 +128,6 @@ cg_growth_run_noalloc = _export("cg_growth_run_noalloc")
 cg_expand = _export("cg_expand")
 cg_hash_insert = _export("cg_hash_insert")
 cg_hash_clear = _export("cg_hash_clear")
+cg_sort_unique_scratch_bytes = _export("cg_sort_unique_scratch_bytes")
+cg_sort_unique = _export("cg_sort_unique")
+cg_set_difference = _export("cg_set_difference")

@@ -18,6 +18,7 @@
 #include "cg_internal.h"
 #include "cg_kernels.h"
 #include "group_order.h"
+#include "sort_kernels.h"
 
 using cg::Ctl;
 using cg::GenSM;
@@ -227,6 +228,17 @@ struct cg_growth {
     uint64_t* d_table = nullptr;
     uint64_t table_slots = 0;
 
+    // sort strategy: three rotating sorted layers, candidate buffer, primitive scratch
+    uint64_t* d_L[3] = {nullptr, nullptr, nullptr};
+    uint64_t L_cap = 0;
+    uint64_t* d_cand = nullptr;
+    uint64_t cand_cap = 0;
+    void* d_sort_scratch = nullptr;
+    unsigned long long* d_count = nullptr;
+    uint64_t* last_layer_ptr = nullptr;   // device pointer of the last reported layer
+    uint64_t last_layer_n = 0;
+    std::vector<uint64_t> sort_layers;
+
     JobDev host_job{};
     bool have_last = false;
     cg_growth_stats stats{};
@@ -243,6 +255,16 @@ struct cg_growth {
         d_gens = nullptr; d_job = nullptr; d_ctl = nullptr; d_ubeg = nullptr;
         d_layers = nullptr; d_keys = nullptr; d_table = nullptr;
         keys_cap = table_slots = 0;
+        release_sort(st);
+    }
+
+    void release_sort(cudaStream_t st) {
+        for (auto& p : d_L) { dev_free(p, st); p = nullptr; }
+        dev_free(d_cand, st);
+        dev_free(d_sort_scratch, st);
+        dev_free(d_count, st);
+        d_cand = nullptr; d_sort_scratch = nullptr; d_count = nullptr;
+        L_cap = cand_cap = 0;
     }
 };
 
@@ -382,6 +404,137 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     h->stats.table_slots = h->table_slots;
     h->host_job = J;
     *final_status = J.status;
+    h->last_layer_ptr = h->d_keys + J.lo;
+    h->last_layer_n = J.hi - J.lo;
+    return CG_OK;
+}
+
+// ---- sort strategy driver ------------------------------------------------------------------
+// Layers live in three rotating buffers sorted ascending; each layer step is expand, radix
+// sort, unique + merge-path difference against layers r and r-1, compaction (sort_path.cu).
+// The host reads |L_{r+1}| after each step to size the next one.
+
+int ensure_sort_buffers(cg_growth* h, uint64_t need_layer, uint64_t need_cand, uint64_t mem,
+                        cudaStream_t st, int cur, int prev, uint64_t Fcur, uint64_t Fprev) {
+    // grow candidate buffer + scratch
+    if (need_cand > h->cand_cap) {
+        uint64_t cap = std::max<uint64_t>(need_cand, std::min<uint64_t>(need_cand * 2, 1ull << 31));
+        cap = std::min<uint64_t>(cap, 0xFFFFFFFFull);
+        const size_t sb = cg::sort_scratch_bytes(cap);
+        const uint64_t layer_bytes = 3 * std::max(h->L_cap, need_layer) * 8;
+        if (cap * 8 + sb + layer_bytes > mem) {
+            cap = need_cand;
+            if (cap * 8 + cg::sort_scratch_bytes(cap) + layer_bytes > mem) return CG_TRUNC_MEMCAP;
+        }
+        dev_free(h->d_cand, st);
+        dev_free(h->d_sort_scratch, st);
+        h->d_cand = (uint64_t*)dev_alloc(cap * 8, st);
+        h->d_sort_scratch = dev_alloc(cg::sort_scratch_bytes(cap), st);
+        h->cand_cap = cap;
+        if (!h->d_cand || !h->d_sort_scratch) return CG_ENOMEM;
+    }
+    if (need_layer > h->L_cap) {
+        uint64_t cap = std::max<uint64_t>(need_layer, std::min<uint64_t>(need_layer * 2, h->order));
+        if (3 * cap * 8 + h->cand_cap * 8 + cg::sort_scratch_bytes(h->cand_cap) > mem) cap = need_layer;
+        if (3 * cap * 8 + h->cand_cap * 8 + cg::sort_scratch_bytes(h->cand_cap) > mem) return CG_TRUNC_MEMCAP;
+        for (int i = 0; i < 3; ++i) {
+            uint64_t* nb = (uint64_t*)dev_alloc(cap * 8, st);
+            if (!nb) return CG_ENOMEM;
+            const uint64_t keep = (i == cur) ? Fcur : (i == prev ? Fprev : 0);
+            if (keep && h->d_L[i]) {
+                cudaError_t e = cudaMemcpyAsync(nb, h->d_L[i], keep * 8, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_rc(e);
+            }
+            dev_free(h->d_L[i], st);
+            h->d_L[i] = nb;
+        }
+        h->L_cap = cap;
+    }
+    return CG_OK;
+}
+
+int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
+    int rc = ensure_small_buffers(h, st);
+    if (rc) return rc;
+    if (!h->d_count) {
+        h->d_count = (unsigned long long*)dev_alloc(64, st);
+        if (!h->d_count) return CG_ENOMEM;
+    }
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    const int bits = 4 * h->n;
+    int cur = 0, prev = 1, nxt = 2;
+    uint64_t Fcur = 1, Fprev = 0;
+    h->sort_layers.assign(1, 1);
+    rc = ensure_sort_buffers(h, 1, std::max<uint64_t>(h->k, 1), mem, st, cur, prev, 0, 0);
+    if (rc) return rc < 0 ? rc : CG_ENOMEM;
+    uint64_t id = 0;
+    for (int i = 0; i < h->n; ++i) id |= (uint64_t)i << (4 * i);
+    cudaError_t e = cudaMemcpyAsync(h->d_L[cur], &id, 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    h->stats.h2d_bytes += 8;
+    if (!h->ev0) {
+        if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
+    }
+    int status = cg::kRunning;
+    int radius = 0;
+    while (status == cg::kRunning) {
+        if (h->max_radius >= 0 && radius >= h->max_radius) { status = cg::kTruncRadius; break; }
+        const uint64_t C = (uint64_t)h->k * Fcur;
+        if (C >= 0xFFFFFFFFull) { status = cg::kNeedMem; break; }
+        rc = ensure_sort_buffers(h, Fcur, C, mem, st, cur, prev, Fcur, Fprev);
+        if (rc == CG_TRUNC_MEMCAP) { status = cg::kNeedMem; break; }
+        if (rc) return rc;
+        cg::SortScratch sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
+        if ((e = cudaMemsetAsync(sc.err, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cg::launch_expand_all(h->d_gens, h->k, h->d_L[cur], Fcur, h->d_cand, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cg::launch_radix_sort(h->d_cand, C, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+        const uint64_t* bs[2] = {h->d_L[cur], h->d_L[prev]};
+        const unsigned long long nbs[2] = {Fcur, Fprev};
+        if ((e = cg::launch_unique_difference(h->d_cand, C, bs, nbs, 2, sc.keys_tmp, h->d_count, sc, st)) !=
+            cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
+        const int passes = (bits + 7) / 8;
+        h->stats.launches += 1 + 3 * passes + 2 + 1;
+        unsigned long long Fn = 0;
+        int derr = 0;
+        if ((e = cudaMemcpyAsync(&Fn, h->d_count, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(&derr, sc.err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.d2h_bytes += 12;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->stats.kernel_ms += ms;
+        h->stats.rounds += 1;
+        if (derr) return derr;
+        if (Fn == 0) { status = cg::kDone; break; }
+        // place L_{r+1} in the free layer buffer
+        rc = ensure_sort_buffers(h, Fn, C, mem, st, cur, prev, Fcur, Fprev);
+        if (rc == CG_TRUNC_MEMCAP) { status = cg::kNeedMem; break; }
+        if (rc) return rc;
+        sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
+        if ((e = cudaMemcpyAsync(h->d_L[nxt], sc.keys_tmp, Fn * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+        h->sort_layers.push_back(Fn);
+        ++radius;
+        const int old_prev = prev;
+        prev = cur;
+        cur = nxt;
+        nxt = old_prev;
+        Fprev = Fcur;
+        Fcur = Fn;
+        if (h->stop_above > 0 && Fn > h->stop_above) { status = cg::kTruncAbove; break; }
+        if ((int)h->sort_layers.size() >= cg::kMaxLayers) { status = cg::kTruncRadius; break; }
+    }
+    h->host_job.radius = radius;
+    h->host_job.status = status;
+    h->last_layer_ptr = h->d_L[cur];
+    h->last_layer_n = Fcur;
+    h->stats.state_capacity = h->L_cap;
+    h->stats.table_slots = 0;
+    *final_status = status;
     return CG_OK;
 }
 
@@ -466,14 +619,19 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
     if (h->device >= 0 && h->device != dev) return CG_EINVAL;
     h->device = dev;
     int status = 0;
-    int rc = run_hash(h, st, &status);
+    const bool use_sort = h->strategy == CG_STRATEGY_SORT;
+    int rc = use_sort ? run_sort(h, st, &status) : run_hash(h, st, &status);
     if (rc) return rc;
     const int layers = h->host_job.radius + 1;
     *num_layers_out = layers;
     if (cap < layers) return CG_EINVAL;
-    e = cudaMemcpyAsync(layer_sizes_out, h->d_layers, sizeof(uint64_t) * layers,
-                        cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_rc(e);
+    if (use_sort) {
+        for (int r = 0; r < layers; ++r) layer_sizes_out[r] = h->sort_layers[r];
+    } else {
+        e = cudaMemcpyAsync(layer_sizes_out, h->d_layers, sizeof(uint64_t) * layers,
+                            cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_rc(e);
+    }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
     h->stats.d2h_bytes += sizeof(uint64_t) * layers;
     h->have_last = true;
@@ -482,10 +640,10 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
 
 int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64_t* count_out) {
     if (!h || !count_out || !h->have_last) return CG_EINVAL;
-    const uint64_t lo = h->host_job.lo, hi = h->host_job.hi;
-    *count_out = hi - lo;
-    if (cap < hi - lo || (!keys_out && hi > lo)) return CG_EINVAL;
-    cudaError_t e = cudaMemcpy(keys_out, h->d_keys + lo, (hi - lo) * 8, cudaMemcpyDeviceToHost);
+    const uint64_t cnt = h->last_layer_n;
+    *count_out = cnt;
+    if (cap < cnt || (!keys_out && cnt > 0)) return CG_EINVAL;
+    cudaError_t e = cudaMemcpy(keys_out, h->last_layer_ptr, cnt * 8, cudaMemcpyDeviceToHost);
     return cuda_rc(e);
 }
 
@@ -547,6 +705,41 @@ int cg_expand(int n, int k, const uint8_t* gens, const uint64_t* frontier, uint6
     if (e == cudaSuccess) e = cg::launch_expand(d, k, frontier, F, out, 152 * 8, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // g is host stack memory
     dev_free(d, st);
+    return cuda_rc(e);
+}
+
+size_t cg_sort_unique_scratch_bytes(uint64_t n) { return cg::sort_scratch_bytes(n); }
+
+int cg_sort_unique(uint64_t* keys, uint64_t n, int key_bits, uint64_t* out, uint64_t* d_count,
+                   void* scratch, size_t scratch_bytes, void* cuda_stream) {
+    if (key_bits < 1 || key_bits > 64 || !d_count || n >= 0xFFFFFFFFull) return CG_EINVAL;
+    if (n > 0 && (!keys || !out || !scratch)) return CG_EINVAL;
+    if (n > 0 && scratch_bytes < cg::sort_scratch_bytes(n)) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (n == 0) return cuda_rc(cudaMemsetAsync(d_count, 0, 8, st));
+    cg::SortScratch sc = cg::carve_sort_scratch(scratch, n);
+    cudaError_t e = cudaMemsetAsync(sc.err, 0, 4, st);
+    if (e == cudaSuccess) e = cg::launch_radix_sort(keys, n, key_bits, sc, st);
+    if (e == cudaSuccess)
+        e = cg::launch_unique_difference(keys, n, nullptr, nullptr, 0, out,
+                                         (unsigned long long*)d_count, sc, st);
+    return cuda_rc(e);
+}
+
+int cg_set_difference(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
+                      const uint64_t* c, uint64_t nc, uint64_t* out, uint64_t* d_count,
+                      void* scratch, size_t scratch_bytes, void* cuda_stream) {
+    if (!d_count || na >= 0xFFFFFFFFull) return CG_EINVAL;
+    if ((na > 0 && (!a || !out || !scratch)) || (nb > 0 && !b) || (nc > 0 && !c)) return CG_EINVAL;
+    if (na > 0 && scratch_bytes < cg::sort_scratch_bytes(na)) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (na == 0) return cuda_rc(cudaMemsetAsync(d_count, 0, 8, st));
+    cg::SortScratch sc = cg::carve_sort_scratch(scratch, na);
+    const uint64_t* bs[2] = {b, c};
+    const unsigned long long ns[2] = {nb, nc};
+    cudaError_t e = cudaMemsetAsync(sc.err, 0, 4, st);
+    if (e == cudaSuccess)
+        e = cg::launch_unique_difference(a, na, bs, ns, 2, out, (unsigned long long*)d_count, sc, st);
     return cuda_rc(e);
 }
 
