@@ -47,10 +47,15 @@ extern "C" {
                                   cg_growth_run_noalloc (CG_NOALLOC_MAX_*)                    */
 
 /* ---- strategies (cg_growth_set_option(h, CG_OPT_STRATEGY, ...)) --------------------- */
-#define CG_STRATEGY_AUTO    0  /* library chooses                                             */
+#define CG_STRATEGY_AUTO    0  /* library chooses: BITMAP when eligible, else HASH            */
 #define CG_STRATEGY_HASH    1  /* visited open-addressing hash set; any generating set        */
 #define CG_STRATEGY_SORT    2  /* sorted layers, radix sort + unique + merge-path difference
                                   against layers r and r-1; inverse-closed sets only          */
+#define CG_STRATEGY_BITMAP  3  /* visited set = one bit per element of S_n, indexed by Lehmer
+                                  rank; any generating set; needs n <= 14 and a bitmap of at
+                                  most half of mem_cap and 16 GiB (else CG_EINVAL at run).
+                                  AUTO picks it when it fits and the group fills at least 1/512
+                                  of S_n, else HASH                                           */
 
 /* ---- options ------------------------------------------------------------------------ */
 #define CG_OPT_STRATEGY     1  /* one of CG_STRATEGY_*                                        */

@@ -27,6 +27,7 @@ CG_ETOOBIG = -7
 CG_STRATEGY_AUTO = 0
 CG_STRATEGY_HASH = 1
 CG_STRATEGY_SORT = 2
+CG_STRATEGY_BITMAP = 3
 
 CG_OPT_STRATEGY = 1
 CG_OPT_STOP_ABOVE = 2

@@ -200,6 +200,52 @@ __device__ __forceinline__ void table_insert_multi_slot(uint64_t* table, uint64_
         if (pend >> i & 1u) res[i] = -1;
 }
 
+// Lehmer rank of the permutation packed in `key` (element i in nibble i), a bijection of S_n
+// onto [0, n!): digit c_i = number of elements after position i that are smaller than p[i],
+// i.e. p[i] minus the smaller values already used; rank = sum c_i (n-1-i)!, evaluated in
+// Horner form.
+__device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
+    unsigned used = 0;
+    uint64_t r = 0;
+    for (int i = 0; i < n; ++i) {
+        const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+        const unsigned c = v - __popc(used & ((1u << v) - 1u));
+        used |= 1u << v;
+        r = r * (uint64_t)(n - i) + c;
+    }
+    return r;
+}
+
+// Visited test-and-set of G keys in a rank-indexed bitmap (one bit per element of S_n).  A
+// plain L2 load first, so that keys already visited cost no atomic; then atomicOr decides the
+// race between equal keys.  res[i] = 1 if this call set the bit, 0 if it was set, -1 if the
+// rank fell outside the bitmap (not a permutation of 0..n-1).
+template <int G>
+__device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words, int n,
+                                                    const uint64_t (&key)[G], int (&res)[G],
+                                                    int nvalid) {
+    uint64_t w[G];
+    unsigned bit[G], v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        res[i] = 0;
+        const uint64_t r = perm_rank(key[i], n);
+        w[i] = r >> 5;
+        bit[i] = 1u << (unsigned)(r & 31u);
+        if (i < nvalid && w[i] >= words) res[i] = -1;
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+        if (i < nvalid && res[i] == 0) v[i] = __ldcg(bm + w[i]);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        if (i < nvalid && res[i] == 0 && !(v[i] & bit[i])) {
+            const unsigned old = atomicOr(bm + w[i], bit[i]);
+            res[i] = (old & bit[i]) ? 0 : 1;
+        }
+    }
+}
+
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  Waits are bounded by
 // `timeout_ns` of wall time; on timeout the error word is set to CG_ETIMEOUT and false is
 // returned, as it is when another block has already set the error word.  Callers return

@@ -21,6 +21,9 @@ struct GenSM {
     uint64_t mask[kMaxN];
 };
 
+constexpr int kVisitHash = 0;
+constexpr int kVisitBitmap = 2;
+
 enum JobStatus : int {
     kRunning = 0,
     kDone = 1,          // empty next layer: growth complete
@@ -46,6 +49,9 @@ struct alignas(128) JobDev {
     int n;
     int layers_cap;
     int max_radius;            // < 0: unlimited
+    int mode;                  // visited set: 0 hash table, 2 rank bitmap (kVisitBitmap)
+    int pad0;
+    uint64_t bitmap_words;     // bitmap mode: 32-bit words in `table` (ceil(n!/32))
     // dynamic, updated between rounds by block 0
     alignas(128) unsigned long long lo;     // frontier = keys[lo, hi)
     unsigned long long hi;

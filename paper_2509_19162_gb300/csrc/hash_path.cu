@@ -130,7 +130,7 @@ __device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, 
 // One unit = 32 frontier states (one per lane) of job J, every generator applied to each:
 // expand, insert-if-absent into the visited table, stage the winners.  kProbeILP generators
 // are handled together (that many independent probe sequences in flight per thread).
-template <int kProbeILP, bool kSector>
+template <int kProbeILP, int kMode>
 __device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsigned long long hi,
                                         uint64_t* buf, int& cnt, int lane, bool& overflow_seen) {
     const bool active = idx < hi;
@@ -143,7 +143,10 @@ __device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsig
         int res[kProbeILP];
 #pragma unroll
         for (int i = 0; i < kProbeILP; ++i) t[i] = (i < ng) ? apply_gen(gens[g0 + i], s) : 0;
-        if (kSector)
+        if (kMode == kVisitBitmap)
+            bitmap_insert_multi<kProbeILP>(reinterpret_cast<unsigned*>(J->table), J->bitmap_words,
+                                           J->n, t, res, active ? ng : 0);
+        else if (kMode == 1)
             table_insert_multi_sector<kProbeILP>(J->table, J->table_mask, t, res, active ? ng : 0,
                                                  kMaxProbe);
         else
@@ -167,8 +170,8 @@ __device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsig
     }
 }
 
-template <int kProbeILP, bool kSector>
-__global__ void __launch_bounds__(kGrowBlock, (kSector && kProbeILP >= 3) ? 2 : 3)
+template <int kProbeILP, int kMode>
+__global__ void __launch_bounds__(kGrowBlock, (kMode == 1 && kProbeILP >= 3) ? 2 : 3)
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
                  uint64_t timeout_ns) {
     __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
@@ -189,7 +192,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
             const unsigned long long hi = ld_relaxed_ull(&J->hi);
             unsigned iter = 0;
             for (unsigned long long b = warp0; b < total; b += nwarps) {
-                do_unit<kProbeILP, kSector>(J, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen);
+                do_unit<kProbeILP, kMode>(J, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen);
                 // Stop early once any warp found the job's buffers full (the layer will be
                 // redone after the host grows them).
                 if ((++iter & 15u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
@@ -212,7 +215,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     u0 = ld_relaxed_ull(ubeg + j);
                 }
                 if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
-                do_unit<kProbeILP, kSector>(J, lo + ((u - u0) << 5) + lane, hi, buf, cnt, lane, overflow_seen);
+                do_unit<kProbeILP, kMode>(J, lo + ((u - u0) << 5) + lane, hi, buf, cnt, lane, overflow_seen);
             }
             if (J) stage_flush(buf, cnt, J, lane);
         }
@@ -230,7 +233,8 @@ __global__ void init_jobs_kernel(JobDev* jobs, int njobs) {
     uint64_t id = 0;
     for (int i = 0; i < J.n; ++i) id |= (uint64_t)i << (4 * i);
     J.keys[0] = id;
-    table_insert(J.table, J.table_mask, id, kMaxProbe);
+    if (J.mode == kVisitBitmap) atomicOr(reinterpret_cast<unsigned*>(J.table), 1u);  // rank(e) = 0
+    else table_insert(J.table, J.table_mask, id, kMaxProbe);
     J.layer_sizes[0] = 1;
     J.lo = 0;
     J.hi = 1;
@@ -265,6 +269,17 @@ __global__ void rebuild_table_kernel(const uint64_t* keys, unsigned long long co
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          i < count; i += (unsigned long long)gridDim.x * blockDim.x) {
         if (table_insert(table, mask, __ldcg(keys + i), kMaxProbe) < 0) atomicExch(err, CG_EDEVICE);
+    }
+}
+
+// Set the bits of keys[0, count) in a (cleared) rank bitmap; used after the key array grew.
+__global__ void rebuild_bitmap_kernel(const uint64_t* keys, unsigned long long count, unsigned* bm,
+                                      uint64_t words, int n, int* err) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         i < count; i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint64_t r = perm_rank(__ldcg(keys + i), n);
+        if ((r >> 5) < words) atomicOr(bm + (r >> 5), 1u << (unsigned)(r & 31u));
+        else atomicExch(err, CG_EDEVICE);
     }
 }
 
@@ -315,17 +330,22 @@ int hash_grow_block() { return kGrowBlock; }
 
 namespace {
 using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t);
-// Probe variants: `ilp` generators per thread (1..4); +8 selects whole-sector probing.
+// Kernel variants: `ilp` generators per thread (1..4); +8 selects whole-sector table probing,
+// +16 the rank bitmap.
 GrowFn grow_fn(int variant) {
     switch (variant) {
-        case 1: return hash_grow_kernel<1, false>;
-        case 2: return hash_grow_kernel<2, false>;
-        case 3: return hash_grow_kernel<3, false>;
-        case 4: return hash_grow_kernel<4, false>;
-        case 9: return hash_grow_kernel<1, true>;
-        case 10: return hash_grow_kernel<2, true>;
-        case 11: return hash_grow_kernel<3, true>;
-        default: return hash_grow_kernel<4, true>;
+        case 1: return hash_grow_kernel<1, 0>;
+        case 2: return hash_grow_kernel<2, 0>;
+        case 3: return hash_grow_kernel<3, 0>;
+        case 4: return hash_grow_kernel<4, 0>;
+        case 9: return hash_grow_kernel<1, 1>;
+        case 10: return hash_grow_kernel<2, 1>;
+        case 11: return hash_grow_kernel<3, 1>;
+        case 12: return hash_grow_kernel<4, 1>;
+        case 17: return hash_grow_kernel<1, 2>;
+        case 18: return hash_grow_kernel<2, 2>;
+        case 19: return hash_grow_kernel<3, 2>;
+        default: return hash_grow_kernel<4, 2>;
     }
 }
 }  // namespace
@@ -372,6 +392,13 @@ cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count,
                                  uint64_t mask, int* d_err, int grid, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     rebuild_table_kernel<<<grid, 256, 0, st>>>(keys, count, table, mask, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild_bitmap(const uint64_t* keys, unsigned long long count, unsigned* bm,
+                                  uint64_t words, int n, int* d_err, int grid, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    rebuild_bitmap_kernel<<<grid, 256, 0, st>>>(keys, count, bm, words, n, d_err);
     return cudaGetLastError();
 }
 

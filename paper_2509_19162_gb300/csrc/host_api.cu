@@ -156,6 +156,28 @@ uint64_t table_slots_for(uint64_t cap) {
 
 uint64_t bytes_for(uint64_t cap) { return cap * 8 + table_slots_for(cap) * 8; }
 
+uint64_t factorial(int n) {
+    uint64_t f = 1;
+    for (int i = 2; i <= n; ++i) f *= (uint64_t)i;
+    return f;
+}
+
+// 32-bit words of a rank bitmap over S_n, rounded up to whole 8-byte slots.
+uint64_t bitmap_words(int n) { return ((factorial(n) + 63) / 64) * 2; }
+
+// The rank bitmap (one bit per element of S_n) replaces the hash table when it fits and is not
+// much larger than a table for the group: n <= 14, at most half of mem_cap and 16 GiB, and the
+// group fills at least 1/512 of S_n.
+bool bitmap_fits(int n, uint64_t mem) {
+    if (n < 2 || n > 14) return false;
+    const uint64_t bytes = bitmap_words(n) * 4;
+    return bytes <= mem / 2 && bytes <= (16ull << 30);
+}
+
+bool bitmap_eligible(int n, uint64_t order, uint64_t mem) {
+    return bitmap_fits(n, mem) && order * 512 >= factorial(n);
+}
+
 // Largest state capacity whose keys + table fit in `mem` bytes.
 uint64_t max_cap_for_mem(uint64_t mem) {
     uint64_t best = 0;
@@ -186,12 +208,12 @@ int status_to_rc(int status) {
     }
 }
 
-int device_grid_cache[64][16] = {};
+int device_grid_cache[64][32] = {};
 
-// Blocks of the persistent kernel that fit co-resident on device `dev` (probe variant: ILP
-// 1..4, +8 for whole-sector probing).
+// Blocks of the persistent kernel that fit co-resident on device `dev` (variant: ILP 1..4, +8
+// for whole-sector table probing, +16 for the rank bitmap).
 int grow_grid(int dev, int ilp) {
-    if (dev < 0 || dev >= 64 || ilp < 1 || ilp > 12) return 0;
+    if (dev < 0 || dev >= 64 || ilp < 1 || ilp > 20) return 0;
     if (!device_grid_cache[dev][ilp]) device_grid_cache[dev][ilp] = cg::hash_grow_max_grid(dev, ilp);
     return device_grid_cache[dev][ilp];
 }
@@ -214,6 +236,7 @@ struct cg_growth {
     int keep_last = 0;
     int grid_override = 0;
     int ilp_override = 0;
+    int mode = -1;                               // visited set chosen at the first run
     uint64_t order = 1;
     int device = -1;
     cudaStream_t alloc_stream = nullptr;
@@ -290,6 +313,21 @@ int ensure_small_buffers(cg_growth* h, cudaStream_t st) {
 int resize_state(cg_growth* h, uint64_t cap, uint64_t keep, cudaStream_t st) {
     uint64_t* keys = (uint64_t*)dev_alloc(cap * 8, st);
     if (!keys) return CG_ENOMEM;
+    if (h->mode == cg::kVisitBitmap) {   // the bitmap has a fixed size: allocate it once
+        if (!h->d_table) {
+            h->table_slots = bitmap_words(h->n) / 2;
+            h->d_table = (uint64_t*)dev_alloc(h->table_slots * 8, st);
+            if (!h->d_table) { dev_free(keys, st); return CG_ENOMEM; }
+        }
+        if (keep > 0) {
+            cudaError_t e = cudaMemcpyAsync(keys, h->d_keys, keep * 8, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) { dev_free(keys, st); return cuda_rc(e); }
+        }
+        dev_free(h->d_keys, st);
+        h->d_keys = keys;
+        h->keys_cap = cap;
+        return CG_OK;
+    }
     const uint64_t slots = table_slots_for(cap);
     uint64_t* table = (uint64_t*)dev_alloc(slots * 8, st);
     if (!table) { dev_free(keys, st); return CG_ENOMEM; }
@@ -318,6 +356,8 @@ void fill_static(cg_growth* h, JobDev& J) {
     J.n = h->n;
     J.layers_cap = cg::kMaxLayers;
     J.max_radius = h->max_radius;
+    J.mode = h->mode;
+    J.bitmap_words = h->mode == cg::kVisitBitmap ? bitmap_words(h->n) : 0;
 }
 
 int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
@@ -326,17 +366,28 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     if (rc) return rc;
     if (fresh_alloc) h->stats.h2d_bytes += sizeof(GenSM) * h->k;
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
-    const uint64_t max_cap = std::min<uint64_t>(h->order, max_cap_for_mem(mem > (1 << 20) ? mem - (1 << 20) : mem));
+    if (h->mode < 0) {
+        if (h->strategy == CG_STRATEGY_BITMAP && !bitmap_fits(h->n, mem)) return CG_EINVAL;
+        h->mode = (h->strategy == CG_STRATEGY_BITMAP ||
+                   (h->strategy == CG_STRATEGY_AUTO && bitmap_eligible(h->n, h->order, mem)))
+                      ? cg::kVisitBitmap : cg::kVisitHash;
+    }
+    const bool bitmap = h->mode == cg::kVisitBitmap;
+    const uint64_t avail = mem > (1 << 20) ? mem - (1 << 20) : mem;
+    const uint64_t bm_bytes = bitmap ? bitmap_words(h->n) * 4 : 0;
+    const uint64_t max_cap = std::min<uint64_t>(
+        h->order, bitmap ? (avail > bm_bytes ? (avail - bm_bytes) / 8 : 0) : max_cap_for_mem(avail));
     if (max_cap < 1) return CG_ENOMEM;
     if (!h->d_keys) {
         uint64_t start = h->order;
-        if (bytes_for(start) > std::min<uint64_t>(mem, kExactAllocLimit))
+        const uint64_t need = bitmap ? start * 8 + bm_bytes : bytes_for(start);
+        if (need > std::min<uint64_t>(mem, kExactAllocLimit))
             start = std::min<uint64_t>(max_cap, 1ull << 24);
         start = std::min(start, max_cap);
         rc = resize_state(h, std::max<uint64_t>(start, 1), 0, st);
         if (rc) return rc;
     }
-    const int ilp = h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k);
+    const int ilp = (h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k)) + (bitmap ? 16 : 0);
     const int grid_max = grow_grid(h->device, ilp);
     if (grid_max <= 0) return CG_ECUDA;
     // Small groups finish faster with fewer blocks at each barrier.
@@ -344,7 +395,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     int grid = (int)std::min<uint64_t>((uint64_t)grid_max, std::max<uint64_t>(want, 1));
     if (h->grid_override > 0) grid = std::min(grid_max, h->grid_override);
 
-    cudaError_t e = cudaMemsetAsync(h->d_table, 0xFF, h->table_slots * 8, st);
+    cudaError_t e = cudaMemsetAsync(h->d_table, bitmap ? 0 : 0xFF, h->table_slots * 8, st);
     if (e != cudaSuccess) return cuda_rc(e);
     JobDev J;
     std::memset(&J, 0, sizeof(J));
@@ -384,11 +435,13 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         const uint64_t keep = J.hi;
         const uint64_t newcap = std::min<uint64_t>(max_cap, std::max<uint64_t>(h->keys_cap * 4, keep + 1));
         if ((rc = resize_state(h, newcap, keep, st))) return rc;
-        if ((e = cudaMemsetAsync(h->d_table, 0xFF, h->table_slots * 8, st)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(h->d_table, bitmap ? 0 : 0xFF, h->table_slots * 8, st)) != cudaSuccess)
             return cuda_rc(e);
-        if ((e = cg::launch_rebuild_table(h->d_keys, keep, h->d_table, h->table_slots - 1,
-                                          &h->d_ctl->err, grid_max, st)) != cudaSuccess)
-            return cuda_rc(e);
+        e = bitmap ? cg::launch_rebuild_bitmap(h->d_keys, keep, reinterpret_cast<unsigned*>(h->d_table),
+                                               bitmap_words(h->n), h->n, &h->d_ctl->err, grid_max, st)
+                   : cg::launch_rebuild_table(h->d_keys, keep, h->d_table, h->table_slots - 1,
+                                              &h->d_ctl->err, grid_max, st);
+        if (e != cudaSuccess) return cuda_rc(e);
         fill_static(h, J);
         J.tail = J.hi;
         J.overflow = 0;
@@ -577,8 +630,13 @@ int cg_growth_set_option(cg_growth_t h, int option, int64_t value) {
     if (!h) return CG_EINVAL;
     switch (option) {
         case CG_OPT_STRATEGY:
-            if (value < CG_STRATEGY_AUTO || value > CG_STRATEGY_SORT) return CG_EINVAL;
+            if (value < CG_STRATEGY_AUTO || value > CG_STRATEGY_BITMAP) return CG_EINVAL;
             if (value == CG_STRATEGY_SORT && !h->inverse_closed) return CG_EINVAL;
+            if (value != h->strategy && h->device >= 0) {   // buffers are laid out per strategy
+                h->release(nullptr);
+                cudaStreamSynchronize(nullptr);
+            }
+            h->mode = -1;
             h->strategy = (int)value;
             return CG_OK;
         case CG_OPT_STOP_ABOVE:
@@ -776,6 +834,7 @@ struct cg_batch {
     };
     std::vector<Job> jobs;
     uint64_t mem_cap = kDefaultMemCap;
+    int mode = cg::kVisitHash;     // one visited-set kind for the whole batch
 };
 
 namespace {
@@ -793,11 +852,12 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     auto al = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
     uint64_t ngens = 0, nkeys = 0, nslots = 0;
     std::vector<uint64_t> goff(nj), koff(nj), toff(nj), slots(nj);
+    const bool bitmap = b->mode == cg::kVisitBitmap;
     for (int i = 0; i < nj; ++i) {
         const auto& J = b->jobs[ids[i]];
         goff[i] = ngens; ngens += J.gsm.size();
         koff[i] = nkeys; nkeys += J.cap;
-        slots[i] = table_slots_for(J.cap);
+        slots[i] = bitmap ? bitmap_words(J.n) / 2 : table_slots_for(J.cap);
         toff[i] = nslots; nslots += slots[i];
     }
     const int lcap = cap + 1;
@@ -830,6 +890,8 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
         D.n = J.n;
         D.layers_cap = lcap;
         D.max_radius = J.max_radius;
+        D.mode = b->mode;
+        D.bitmap_words = bitmap ? bitmap_words(J.n) : 0;
     }
     JobDev* d_jobs = (JobDev*)(base + o_jobs);
     unsigned long long* d_ubeg = (unsigned long long*)(base + o_ubeg);
@@ -837,7 +899,7 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     cudaError_t e = cudaSuccess;
     if (ngens) e = cudaMemcpyAsync(base + o_gens, hg.data(), ngens * sizeof(GenSM), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, hj.data(), nj * sizeof(JobDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tab, 0xFF, nslots * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tab, bitmap ? 0 : 0xFF, nslots * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
     if (e == cudaSuccess)
@@ -911,8 +973,13 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_rc(e);
     int maxk = 1;
-    for (auto& J : b->jobs) maxk = std::max(maxk, J.k);
-    const int ilp = default_ilp(maxk);
+    bool all_bitmap = true;
+    for (auto& J : b->jobs) {
+        maxk = std::max(maxk, J.k);
+        all_bitmap &= (J.k == 0 || (J.n <= 12 && bitmap_eligible(J.n, J.order, b->mem_cap)));
+    }
+    b->mode = all_bitmap ? cg::kVisitBitmap : cg::kVisitHash;
+    const int ilp = default_ilp(maxk) + (all_bitmap ? 16 : 0);
     const int grid = grow_grid(dev, ilp);
     if (grid <= 0) return CG_ECUDA;
     const uint64_t budget = b->mem_cap;
@@ -936,7 +1003,8 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
             continue;
         }
         J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
-        const uint64_t need = bytes_for(J.cap) + sizeof(GenSM) * J.gsm.size() + sizeof(JobDev) +
+        const uint64_t vis = b->mode == cg::kVisitBitmap ? J.cap * 8 + bitmap_words(J.n) * 4 : bytes_for(J.cap);
+        const uint64_t need = vis + sizeof(GenSM) * J.gsm.size() + sizeof(JobDev) +
                               (uint64_t)(cap + 1) * 8 + 1024;
         if (!wave.empty() && wave_bytes + need > budget) flush();
         wave.push_back(j);

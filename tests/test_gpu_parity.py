@@ -51,20 +51,26 @@ def test_s8_coxeter_full(cg):
     assert r.layers == oracle.growth(8, w.coxeter(8))[0]
 
 
-def test_s11_lrx_full(cg):
-    r = cg.growth(11, w.lrx(11))
+STRATS = ["hash", "bitmap", "auto"]
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+def test_s11_lrx_full(cg, strategy):
+    r = cg.growth(11, w.lrx(11), strategy=strategy)
     assert r.status == 0
     assert r.layers == golden("s11_lrx_growth")
     assert r.total == math.factorial(11)
 
 
-def test_s10_lx_directed(cg):
-    r = cg.growth(10, w.lx(10), inverse_closed=False)
+@pytest.mark.parametrize("strategy", STRATS)
+def test_s10_lx_directed(cg, strategy):
+    r = cg.growth(10, w.lx(10), inverse_closed=False, strategy=strategy)
     assert r.layers == golden("s10_lx_growth")
 
 
+@pytest.mark.parametrize("strategy", ["hash", "bitmap"])
 @pytest.mark.parametrize("seed", range(24))
-def test_random_sets_vs_oracle(cg, seed):
+def test_random_sets_vs_oracle(cg, seed, strategy):
     rng = np.random.default_rng(1000 + seed)
     n = int(rng.integers(2, 10))
     k = int(rng.integers(1, 5))
@@ -72,7 +78,7 @@ def test_random_sets_vs_oracle(cg, seed):
     if seed % 2 == 0:
         gens = w.inverse_closure(gens) or gens
     want, _ = oracle.growth(n, gens)
-    got = cg.growth(n, gens)
+    got = cg.growth(n, gens, strategy=strategy)
     assert got.layers == want
     assert got.status == 0
 
@@ -81,12 +87,13 @@ def test_random_sets_vs_oracle(cg, seed):
                                     "lx", "pancake", "reversals", "transposons", "three_cycles",
                                     "cycles_01i_inv", "consecutive_3cycles_inv", "prefix_cycles"])
 @pytest.mark.parametrize("n", [2, 3, 5, 7, 9])
-def test_families_vs_oracle(cg, family, n):
+@pytest.mark.parametrize("strategy", ["hash", "bitmap"])
+def test_families_vs_oracle(cg, family, n, strategy):
     gens = w.FAMILIES[family](n)
     if not gens:
         pytest.skip("empty generating set")
     want, _ = oracle.growth(n, gens)
-    assert cg.growth(n, gens).layers == want
+    assert cg.growth(n, gens, strategy=strategy).layers == want
 
 
 def test_edge_cases(cg):
@@ -113,21 +120,23 @@ def test_radius_and_stop_limits(cg):
     assert r.layers == m[:len(r.layers)]
 
 
-def test_memcap_regrow_and_truncation(cg):
+@pytest.mark.parametrize("strategy", ["hash", "bitmap"])
+def test_memcap_regrow_and_truncation(cg, strategy):
     want = golden("s11_lrx_growth")
-    # mem_cap large enough for the whole growth but forcing grow-and-rebuild steps is exercised
-    # by n = 14 (order too large to allocate up front)
-    r = cg.growth(14, w.pancake(14), max_radius=7)
+    # grow-and-rebuild of the state array (and of the visited set) is exercised by n = 14: the
+    # group order is too large to allocate up front, layers 0..7 hold 16.8M > 2^24 states
+    r = cg.growth(14, w.pancake(14), max_radius=7, strategy=strategy)
     assert r.layers == golden("s14_pancake_layers")[:8]
     # a cap too small for the whole S11 growth: exact prefix, then CG_TRUNC_MEMCAP
-    r = cg.growth(11, w.lrx(11), mem_cap=64 << 20)
+    r = cg.growth(11, w.lrx(11), mem_cap=64 << 20, strategy=strategy)
     assert r.status == 2
     assert r.layers == want[:len(r.layers)] and len(r.layers) < len(want)
 
 
-def test_last_layer_matches_oracle(cg):
+@pytest.mark.parametrize("strategy", ["hash", "bitmap"])
+def test_last_layer_matches_oracle(cg, strategy):
     for n, gens in [(8, w.coxeter(8)), (7, w.reversals(7)), (8, w.lx(8)), (7, w.all_transpositions(7))]:
-        g = cg.Growth(n, gens, keep_last=True)
+        g = cg.Growth(n, gens, keep_last=True, strategy=strategy)
         r = g.run()
         keys = np.sort(g.last_layer())
         want = oracle.layer_keys(n, gens, len(r.layers) - 1)
@@ -142,11 +151,12 @@ def test_last_layer_matches_oracle(cg):
     ("undirected", 12, 95, "(01)(23)(45)(67)(89)(10,11); (12)(35)(46)(78)(9,10); (36)(45)"),
     ("directed", 12, 106, "(01)(23)(45)(67)(89); (1,11,9,10)(04)(28)(36)"),
 ])
-def test_published_max_diameters_gpu(cg, kind, n, d, gens_text):
+@pytest.mark.parametrize("strategy", ["hash", "bitmap"])
+def test_published_max_diameters_gpu(cg, kind, n, d, gens_text, strategy):
     # Section 3.4 tables: the printed diameter and the layer sum n! (these sizes exceed what
     # the oracle finishes in seconds; the pins are the paper's numbers).
     gens = [w.from_cycles(n, t) for t in gens_text.split(";")]
-    r = cg.growth(n, gens, inverse_closed=(kind == "undirected"))
+    r = cg.growth(n, gens, inverse_closed=(kind == "undirected"), strategy=strategy)
     assert r.status == 0
     assert r.diameter == d
     assert r.total == math.factorial(n)
@@ -223,3 +233,13 @@ def test_step_hash_insert_is_set_insert(cg):
         want = np.array(sorted(set(int(x) for x in keys) - seen), dtype=np.uint64)
         assert np.array_equal(new, want)
         seen |= set(int(x) for x in keys)
+
+
+def test_batch_with_hash_visited_sets(cg):
+    # a job with n > 12 makes the whole batch use hash tables instead of rank bitmaps
+    jobs = [(13, w.coxeter(13), True, 6), (9, w.lrx(9), True, -1), (7, w.lx(7), False, -1)]
+    with cg.Batch(jobs) as b:
+        res = b.run()
+    assert res[0].layers == mahonian(13)[:7] and res[0].status == 1
+    assert res[1].layers == oracle.growth(9, w.lrx(9))[0]
+    assert res[2].layers == oracle.growth(7, w.lx(7))[0]
