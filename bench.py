@@ -243,6 +243,11 @@ def run_ours(args):
           for _ in range(args.steps)]
     kernel_ms = 0.0
     launches = 0
+    st0 = handle.stats()
+    strat_name = {1: "hash", 2: "sort", 3: "bitmap"}.get(st0["strategy_used"], "?")
+    variant = st0["probe_variant"]
+    kernel_name = (f"hash_grow_kernel<{variant & 7}, {variant >> 3}>" if strat_name != "sort"
+                   else "radix sort / merge-path kernels")
     for i in range(args.steps):
         flush.zero_()                               # evict L2 between timed steps
         torch.cuda.synchronize()
@@ -299,11 +304,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": job.name, "n": job.n, "k": job.k, "states": sum(layers),
                    "layers": len(layers), "neighbours_per_step": nb_step,
-                   "strategy": "hash (visited table, persistent cooperative kernel)",
+                   "strategy": strat_name + " (visited set; one persistent cooperative launch)",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "hash_grow_kernel",
+                     "frac": achieved / peak, "traffic": None, "kernel": kernel_name,
                      "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
                      "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -139,6 +139,8 @@ typedef struct cg_growth_stats {
     uint64_t d2h_bytes;
     uint64_t state_capacity;    /* states the job's buffers hold */
     uint64_t table_slots;       /* visited-table slots (hash strategy) */
+    int strategy_used;          /* CG_STRATEGY_HASH, _SORT or _BITMAP: what the run used */
+    int probe_variant;          /* kernel variant of the run (generators probed together) */
 } cg_growth_stats;
 int cg_growth_get_stats(cg_growth_t h, cg_growth_stats* out);
 

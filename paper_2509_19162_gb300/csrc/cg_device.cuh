@@ -98,17 +98,16 @@ __device__ __forceinline__ void ld_sector(const uint64_t* p, uint64_t (&v)[4]) {
 // thread keeps G sector loads (and CASes) in flight.  Each step reads the aligned 4-slot
 // sector holding the current slot and scans it from that slot on: a match ends the sequence
 // (already present); the first empty slot gets a CAS; a full sector moves on to the next.
-// res[i] as for table_insert; entries i >= nvalid are left at 0.
+// res[i] as for table_insert; entries whose bit in vmask is clear are left at 0.
 template <int G>
 __device__ __forceinline__ void table_insert_multi_sector(uint64_t* table, uint64_t mask,
                                                           const uint64_t (&key)[G], int (&res)[G],
-                                                          int nvalid, uint64_t max_steps) {
+                                                          unsigned vmask, uint64_t max_steps) {
     uint64_t h[G];
-    unsigned pend = 0;   // bit i: sequence i still probing
+    unsigned pend = vmask;   // bit i: sequence i still probing
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         res[i] = 0;
-        if (i < nvalid) pend |= 1u << i;
         h[i] = mix64(key[i]) & mask;
     }
     for (uint64_t step = 0; pend && step < max_steps; ++step) {
@@ -159,13 +158,12 @@ __device__ __forceinline__ void table_insert_multi_sector(uint64_t* table, uint6
 template <int G>
 __device__ __forceinline__ void table_insert_multi_slot(uint64_t* table, uint64_t mask,
                                                         const uint64_t (&key)[G], int (&res)[G],
-                                                        int nvalid, uint64_t max_steps) {
+                                                        unsigned vmask, uint64_t max_steps) {
     uint64_t h[G];
-    unsigned pend = 0;
+    unsigned pend = vmask;
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         res[i] = 0;
-        if (i < nvalid) pend |= 1u << i;
         h[i] = mix64(key[i]) & mask;
     }
     for (uint64_t step = 0; pend && step < max_steps; ++step) {
@@ -205,13 +203,31 @@ __device__ __forceinline__ void table_insert_multi_slot(uint64_t* table, uint64_
 // i.e. p[i] minus the smaller values already used; rank = sum c_i (n-1-i)!, evaluated in
 // Horner form.
 __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
+    // The last digit is always 0 and is skipped; the loop is unrolled so every nibble shift is
+    // a constant.  For n <= 12 the rank fits in 32 bits.
     unsigned used = 0;
+    if (n <= 12) {
+        unsigned r = 0;
+#pragma unroll
+        for (int i = 0; i < 11; ++i) {
+            if (i < n - 1) {
+                const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+                const unsigned c = v - __popc(used & ((1u << v) - 1u));
+                used |= 1u << v;
+                r = r * (unsigned)(n - i) + c;
+            }
+        }
+        return r;
+    }
     uint64_t r = 0;
-    for (int i = 0; i < n; ++i) {
-        const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-        const unsigned c = v - __popc(used & ((1u << v) - 1u));
-        used |= 1u << v;
-        r = r * (uint64_t)(n - i) + c;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+        if (i < n - 1) {
+            const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+            const unsigned c = v - __popc(used & ((1u << v) - 1u));
+            used |= 1u << v;
+            r = r * (uint64_t)(n - i) + c;
+        }
     }
     return r;
 }
@@ -223,7 +239,7 @@ __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
 template <int G>
 __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words, int n,
                                                     const uint64_t (&key)[G], int (&res)[G],
-                                                    int nvalid) {
+                                                    unsigned vmask) {
     uint64_t w[G];
     unsigned bit[G], v[G];
 #pragma unroll
@@ -232,58 +248,75 @@ __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words
         const uint64_t r = perm_rank(key[i], n);
         w[i] = r >> 5;
         bit[i] = 1u << (unsigned)(r & 31u);
-        if (i < nvalid && w[i] >= words) res[i] = -1;
+        if ((vmask >> i & 1u) && w[i] >= words) res[i] = -1;
     }
 #pragma unroll
     for (int i = 0; i < G; ++i)
-        if (i < nvalid && res[i] == 0) v[i] = __ldcg(bm + w[i]);
+        if ((vmask >> i & 1u) && res[i] == 0) v[i] = __ldcg(bm + w[i]);
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        if (i < nvalid && res[i] == 0 && !(v[i] & bit[i])) {
+        if ((vmask >> i & 1u) && res[i] == 0 && !(v[i] & bit[i])) {
             const unsigned old = atomicOr(bm + w[i], bit[i]);
             res[i] = (old & bit[i]) ? 0 : 1;
         }
     }
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Waits are bounded by
-// `timeout_ns` of wall time; on timeout the error word is set to CG_ETIMEOUT and false is
-// returned, as it is when another block has already set the error word.  Callers return
-// from the kernel on false.
-__device__ __forceinline__ bool grid_barrier(Ctl* ctl, uint64_t timeout_ns) {
-    __shared__ int s_ok;
+// Arrival half of a grid barrier whose last arriving block does some work before releasing
+// the others (cooperative launch: all blocks co-resident).  Returns 1 in every thread of the
+// block that arrived last (it must call grid_release after its work), 0 in the other blocks
+// once the last block has released them, -1 on error (timeout or an error word set by
+// another block: the caller returns from the kernel).
+__device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns) {
+    __shared__ int s_state;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
         volatile unsigned int* vgen = &ctl->bar_gen;
         const unsigned int gen = *vgen;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&ctl->bar_count, 0u);
+        const unsigned g = blockIdx.x % kBarGroups;
+        const unsigned gsize = (gridDim.x - g + kBarGroups - 1) / kBarGroups;
+        const unsigned ngroups = gridDim.x < (unsigned)kBarGroups ? gridDim.x : (unsigned)kBarGroups;
+        int state = 0;
+        if (atomicAdd(&ctl->group[g].count, 1u) == gsize - 1) {
+            atomicExch(&ctl->group[g].count, 0u);
             __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
+            if (atomicAdd(&ctl->bar_count, 1u) == ngroups - 1) {
+                atomicExch(&ctl->bar_count, 0u);
+                __threadfence();
+                state = 1;
+            }
+        }
+        if (state == 0) {
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
             while (*vgen == gen) {
                 if ((++spins & 63u) == 0) {
-                    if (*(volatile int*)&ctl->err != 0) { ok = 0; break; }
+                    if (*(volatile int*)&ctl->err != 0) { state = -1; break; }
                     if (globaltimer_ns() - t0 > timeout_ns) {
                         atomicCAS(&ctl->err, 0, CG_ETIMEOUT);
-                        ok = 0;
+                        state = -1;
                         break;
                     }
                 }
                 __nanosleep(spins < 64 ? 32 : 256);
             }
+            __threadfence();
+            if (state == 0 && *(volatile int*)&ctl->err != 0) state = -1;
         }
-        __threadfence();
-        if (*(volatile int*)&ctl->err != 0) ok = 0;
-        s_ok = ok;
+        s_state = state;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_state;
+}
+
+// Release half: called by every thread of the last arriving block after its work.
+__device__ __forceinline__ void grid_release(Ctl* ctl) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&ctl->bar_gen, 1u);
+    }
 }
 
 }  // namespace cg

@@ -16,10 +16,15 @@ constexpr int kMaxLayers = 16384;    // device layer-size array per job
 // transpositions 3, a prefix reversal of length j needs j+1 at most, any generator <= n.
 struct GenSM {
     uint32_t nterms;
-    uint32_t pad;
+    uint32_t inv_tag;   // 1 + index of this generator's inverse in the set (< 15), or 0
     uint8_t rot[kMaxN];
     uint64_t mask[kMaxN];
 };
+
+// States found by generator j are stored with tag (1 + index of j's inverse) in key bits 60-63
+// when n <= 15: that inverse leads back to the state's parent, in the previous layer, so the
+// expansion skips it.  The visited set always holds untagged keys.
+constexpr uint64_t kKeyBits60 = (1ull << 60) - 1;
 
 constexpr int kVisitHash = 0;
 constexpr int kVisitBitmap = 2;
@@ -63,8 +68,11 @@ struct alignas(128) JobDev {
 };
 
 // Control block of the persistent kernel (device memory, zero-initialised by the host).
-// The barrier's arrival counter and the generation word that waiting blocks poll sit in
-// different 128-byte lines, so polling does not queue behind arrivals at one L2 slice.
+// Blocks arrive at the grid barrier on kBarGroups group counters, the last of each group on
+// the top counter; every counter and the generation word that waiting blocks poll sit in
+// their own 128-byte line, so neither arrivals nor polling queue at one L2 slice.
+constexpr int kBarGroups = 32;
+
 struct alignas(128) Ctl {
     unsigned int bar_count;
     unsigned int pad0[31];
@@ -73,6 +81,11 @@ struct alignas(128) Ctl {
     int err;                        // 0, or a CG_E* code set by a kernel
     int rounds;                     // rounds completed
     unsigned long long total_units; // warp work units of the current round
+    unsigned int pad2[28];
+    struct alignas(128) Group {
+        unsigned int count;
+        unsigned int pad[31];
+    } group[kBarGroups];
 };
 
 }  // namespace cg

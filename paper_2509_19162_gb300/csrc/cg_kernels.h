@@ -19,7 +19,8 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
                              int grid, int max_rounds, uint64_t timeout_ns, int ilp,
                              cudaStream_t st);
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,
-                                 uint64_t mask, int* d_err, int grid, cudaStream_t st);
+                                 uint64_t mask, uint64_t key_mask, int* d_err, int grid,
+                                 cudaStream_t st);
 cudaError_t launch_rebuild_bitmap(const uint64_t* keys, unsigned long long count, unsigned* bm,
                                   uint64_t words, int n, int* d_err, int grid, cudaStream_t st);
 cudaError_t launch_expand(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,

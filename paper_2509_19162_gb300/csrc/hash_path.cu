@@ -35,8 +35,8 @@ __device__ __forceinline__ int find_job(const unsigned long long* ubeg, int njob
     return lo;
 }
 
-// Phase B, executed by block 0 only: close the layer of every running job and lay out the
-// work of the next round.  ubeg has njobs + 1 entries.
+// Phase B, executed by the block that arrives last at the round's barrier: close the layer of
+// every running job and lay out the work of the next round.  ubeg has njobs + 1 entries.
 __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl) {
     __shared__ unsigned long long s_warp[kGrowBlock / 32];
     __shared__ unsigned long long s_carry;
@@ -47,28 +47,31 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
         const int j = base + threadIdx.x;
         unsigned long long units = 0;
         if (j < njobs) {
+            // The previous round may have been closed by another SM: read every field that
+            // changes during a run through L2 (volatile), never from this SM's L1.
             JobDev& J = jobs[j];
-            if (J.status == kRunning) {
-                // tail and overflow are updated with atomics by every block: read them from L2.
+            volatile JobDev& V = jobs[j];
+            if (V.status == kRunning) {
                 const unsigned long long tail = ld_relaxed_ull(&J.tail);
+                const unsigned long long hi = V.hi;
                 if (ld_relaxed_int(&J.overflow)) {
-                    J.status = kNeedMem;
+                    V.status = kNeedMem;
                 } else {
-                    const unsigned long long fresh = tail - J.hi;
+                    const unsigned long long fresh = tail - hi;
                     if (fresh == 0) {
-                        J.status = kDone;
+                        V.status = kDone;
                     } else {
-                        const int r = J.radius + 1;
+                        const int r = V.radius + 1;
                         J.layer_sizes[r] = fresh;
-                        J.radius = r;
-                        J.lo = J.hi;
-                        J.hi = tail;
-                        if (J.max_radius >= 0 && r >= J.max_radius) J.status = kTruncRadius;
-                        else if (J.stop_above > 0 && fresh > J.stop_above) J.status = kTruncAbove;
-                        else if (r + 1 >= J.layers_cap) J.status = kTruncRadius;
+                        V.radius = r;
+                        V.lo = hi;
+                        V.hi = tail;
+                        if (J.max_radius >= 0 && r >= J.max_radius) V.status = kTruncRadius;
+                        else if (J.stop_above > 0 && fresh > J.stop_above) V.status = kTruncAbove;
+                        else if (r + 1 >= J.layers_cap) V.status = kTruncRadius;
                     }
                 }
-                if (J.status == kRunning) units = (J.hi - J.lo + 31) >> 5;
+                if (V.status == kRunning) units = (V.hi - V.lo + 31) >> 5;
             }
         }
         // block-wide exclusive scan of units
@@ -99,7 +102,7 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
     if (threadIdx.x == 0) {
         ubeg[njobs] = s_carry;
         ctl->total_units = s_carry;
-        ctl->rounds += 1;
+        atomicAdd(&ctl->rounds, 1);
     }
 }
 
@@ -131,27 +134,35 @@ __device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, 
 // expand, insert-if-absent into the visited table, stage the winners.  kProbeILP generators
 // are handled together (that many independent probe sequences in flight per thread).
 template <int kProbeILP, int kMode>
-__device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsigned long long hi,
-                                        uint64_t* buf, int& cnt, int lane, bool& overflow_seen) {
+__device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned long long idx,
+                                        unsigned long long hi, uint64_t* buf, int& cnt, int lane,
+                                        bool& overflow_seen) {
     const bool active = idx < hi;
-    const uint64_t s = active ? __ldcg(J->keys + idx) : 0;
+    const int n = J->n;
+    uint64_t s = active ? __ldcg(J->keys + idx) : 0;
+    unsigned tag = 0;                       // 1 + generator that leads back to the parent
+    if (n <= 15) {
+        tag = (unsigned)(s >> 60);
+        s &= kKeyBits60;
+    }
     const int k = J->k;
-    const GenSM* gens = J->gens;
     for (int g0 = 0; g0 < k; g0 += kProbeILP) {
         const int ng = min(kProbeILP, k - g0);
         uint64_t t[kProbeILP];
         int res[kProbeILP];
+        unsigned vmask = 0;
 #pragma unroll
-        for (int i = 0; i < kProbeILP; ++i) t[i] = (i < ng) ? apply_gen(gens[g0 + i], s) : 0;
+        for (int i = 0; i < kProbeILP; ++i) {
+            t[i] = (i < ng) ? apply_gen(gens[g0 + i], s) : 0;
+            if (active && i < ng && tag != (unsigned)(g0 + i + 1)) vmask |= 1u << i;
+        }
         if (kMode == kVisitBitmap)
             bitmap_insert_multi<kProbeILP>(reinterpret_cast<unsigned*>(J->table), J->bitmap_words,
-                                           J->n, t, res, active ? ng : 0);
+                                           n, t, res, vmask);
         else if (kMode == 1)
-            table_insert_multi_sector<kProbeILP>(J->table, J->table_mask, t, res, active ? ng : 0,
-                                                 kMaxProbe);
+            table_insert_multi_sector<kProbeILP>(J->table, J->table_mask, t, res, vmask, kMaxProbe);
         else
-            table_insert_multi_slot<kProbeILP>(J->table, J->table_mask, t, res, active ? ng : 0,
-                                               kMaxProbe);
+            table_insert_multi_slot<kProbeILP>(J->table, J->table_mask, t, res, vmask, kMaxProbe);
         bool bad = false;
 #pragma unroll
         for (int i = 0; i < kProbeILP; ++i) bad |= (res[i] < 0);
@@ -162,7 +173,10 @@ __device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsig
 #pragma unroll
         for (int i = 0; i < kProbeILP; ++i) {
             const unsigned fresh = __ballot_sync(0xffffffffu, res[i] == 1);
-            if (res[i] == 1) buf[cnt + __popc(fresh & lanemask_lt())] = t[i];
+            if (res[i] == 1) {
+                const uint64_t itag = (n <= 15 && i < ng) ? (uint64_t)gens[g0 + i].inv_tag << 60 : 0;
+                buf[cnt + __popc(fresh & lanemask_lt())] = t[i] | itag;
+            }
             cnt += __popc(fresh);
             __syncwarp();
             if (cnt > kStage - 32) stage_flush(buf, cnt, J, lane);
@@ -170,11 +184,21 @@ __device__ __forceinline__ void do_unit(JobDev* J, unsigned long long idx, unsig
     }
 }
 
+// Generators of a single job kept in shared memory when there are at most this many.
+constexpr int kSmemGens = 32;
+
 template <int kProbeILP, int kMode>
-__global__ void __launch_bounds__(kGrowBlock, (kMode == 1 && kProbeILP >= 3) ? 2 : 3)
+__global__ void __launch_bounds__(kGrowBlock, kMode == 2 ? 4 : ((kMode == 1 && kProbeILP >= 3) ? 2 : 3))
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
                  uint64_t timeout_ns) {
     __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
+    __shared__ GenSM s_gens[kSmemGens];
+    const GenSM* single_gens = jobs[0].gens;
+    if (njobs == 1 && jobs[0].k <= kSmemGens) {
+        for (int j = threadIdx.x; j < jobs[0].k; j += blockDim.x) s_gens[j] = jobs[0].gens[j];
+        __syncthreads();
+        single_gens = s_gens;
+    }
     const int lane = threadIdx.x & 31;
     uint64_t* buf = s_stage[threadIdx.x >> 5];
     const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
@@ -192,7 +216,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
             const unsigned long long hi = ld_relaxed_ull(&J->hi);
             unsigned iter = 0;
             for (unsigned long long b = warp0; b < total; b += nwarps) {
-                do_unit<kProbeILP, kMode>(J, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen);
+                do_unit<kProbeILP, kMode>(J, single_gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen);
                 // Stop early once any warp found the job's buffers full (the layer will be
                 // redone after the host grows them).
                 if ((++iter & 15u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
@@ -215,13 +239,19 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     u0 = ld_relaxed_ull(ubeg + j);
                 }
                 if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
-                do_unit<kProbeILP, kMode>(J, lo + ((u - u0) << 5) + lane, hi, buf, cnt, lane, overflow_seen);
+                do_unit<kProbeILP, kMode>(J, J->gens, lo + ((u - u0) << 5) + lane, hi, buf, cnt, lane,
+                                          overflow_seen);
             }
             if (J) stage_flush(buf, cnt, J, lane);
         }
-        if (!grid_barrier(ctl, timeout_ns)) return;
-        if (blockIdx.x == 0) close_round(jobs, njobs, ubeg, ctl);
-        if (!grid_barrier(ctl, timeout_ns)) return;
+        // One barrier per round: the last block to finish the round closes it (layer counts,
+        // stop tests, next round's work layout) and then releases the others.
+        const int arrive = grid_arrive(ctl, timeout_ns);
+        if (arrive < 0) return;
+        if (arrive == 1) {
+            close_round(jobs, njobs, ubeg, ctl);
+            grid_release(ctl);
+        }
     }
 }
 
@@ -265,10 +295,11 @@ __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* u
 // Re-insert keys[0, count) of one job into its (cleared) table; used after the key array
 // grew.  Dups cannot occur: the keys are distinct.
 __global__ void rebuild_table_kernel(const uint64_t* keys, unsigned long long count,
-                                     uint64_t* table, uint64_t mask, int* err) {
+                                     uint64_t* table, uint64_t mask, uint64_t key_mask, int* err) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          i < count; i += (unsigned long long)gridDim.x * blockDim.x) {
-        if (table_insert(table, mask, __ldcg(keys + i), kMaxProbe) < 0) atomicExch(err, CG_EDEVICE);
+        if (table_insert(table, mask, __ldcg(keys + i) & key_mask, kMaxProbe) < 0)
+            atomicExch(err, CG_EDEVICE);
     }
 }
 
@@ -277,7 +308,7 @@ __global__ void rebuild_bitmap_kernel(const uint64_t* keys, unsigned long long c
                                       uint64_t words, int n, int* err) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          i < count; i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint64_t r = perm_rank(__ldcg(keys + i), n);
+        const uint64_t r = perm_rank(__ldcg(keys + i) & (n <= 15 ? kKeyBits60 : ~0ull), n);
         if ((r >> 5) < words) atomicOr(bm + (r >> 5), 1u << (unsigned)(r & 31u));
         else atomicExch(err, CG_EDEVICE);
     }
@@ -389,9 +420,10 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
 }
 
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,
-                                 uint64_t mask, int* d_err, int grid, cudaStream_t st) {
+                                 uint64_t mask, uint64_t key_mask, int* d_err, int grid,
+                                 cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    rebuild_table_kernel<<<grid, 256, 0, st>>>(keys, count, table, mask, d_err);
+    rebuild_table_kernel<<<grid, 256, 0, st>>>(keys, count, table, mask, key_mask, d_err);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,20 @@ std::vector<std::vector<uint8_t>> clean_rows(int n, int k, const uint8_t* gens) 
     return out;
 }
 
+// Shift-and-mask forms of distinct rows, with each generator's inverse tag (1 + index of its
+// inverse among the rows when that index is below 15, else 0).
+std::vector<GenSM> make_gensms(const std::vector<std::vector<uint8_t>>& rows, int n) {
+    std::vector<GenSM> out;
+    for (auto& r : rows) out.push_back(make_gensm(r.data(), n));
+    for (size_t j = 0; j < rows.size(); ++j) {
+        std::vector<uint8_t> inv(n);
+        for (int i = 0; i < n; ++i) inv[rows[j][i]] = (uint8_t)i;
+        for (size_t m = 0; m < rows.size() && m < 15; ++m)
+            if (rows[m] == inv) { out[j].inv_tag = (uint32_t)(m + 1); break; }
+    }
+    return out;
+}
+
 bool closed_under_inverse(const std::vector<std::vector<uint8_t>>& rows, int n) {
     std::set<std::vector<uint8_t>> s(rows.begin(), rows.end());
     for (auto& r : rows) {
@@ -440,7 +454,8 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         e = bitmap ? cg::launch_rebuild_bitmap(h->d_keys, keep, reinterpret_cast<unsigned*>(h->d_table),
                                                bitmap_words(h->n), h->n, &h->d_ctl->err, grid_max, st)
                    : cg::launch_rebuild_table(h->d_keys, keep, h->d_table, h->table_slots - 1,
-                                              &h->d_ctl->err, grid_max, st);
+                                              h->n <= 15 ? cg::kKeyBits60 : ~0ull, &h->d_ctl->err,
+                                              grid_max, st);
         if (e != cudaSuccess) return cuda_rc(e);
         fill_static(h, J);
         J.tail = J.hi;
@@ -455,6 +470,8 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     }
     h->stats.state_capacity = h->keys_cap;
     h->stats.table_slots = h->table_slots;
+    h->stats.strategy_used = bitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
+    h->stats.probe_variant = ilp;
     h->host_job = J;
     *final_status = J.status;
     h->last_layer_ptr = h->d_keys + J.lo;
@@ -587,6 +604,8 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
     h->last_layer_n = Fcur;
     h->stats.state_capacity = h->L_cap;
     h->stats.table_slots = 0;
+    h->stats.strategy_used = CG_STRATEGY_SORT;
+    h->stats.probe_variant = 0;
     *final_status = status;
     return CG_OK;
 }
@@ -615,7 +634,7 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
     if (!h) return CG_ENOMEM;
     h->n = n;
     h->k = (int)rows.size();
-    for (auto& r : rows) h->gsm.push_back(make_gensm(r.data(), n));
+    h->gsm = make_gensms(rows, n);
     h->inverse_closed = inverse_closed ? 1 : 0;
     h->max_radius = max_radius < 0 ? -1 : max_radius;
     h->mem_cap = mem_cap ? mem_cap : kDefaultMemCap;
@@ -702,6 +721,8 @@ int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64
     *count_out = cnt;
     if (cap < cnt || (!keys_out && cnt > 0)) return CG_EINVAL;
     cudaError_t e = cudaMemcpy(keys_out, h->last_layer_ptr, cnt * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h->n <= 15)   // strip the parent-edge tags of stored states
+        for (uint64_t i = 0; i < cnt; ++i) keys_out[i] &= cg::kKeyBits60;
     return cuda_rc(e);
 }
 
@@ -956,7 +977,7 @@ int cg_batch_create(int njobs, const int* n, const int* k, const uint8_t* gens,
         J.n = n[j];
         J.k = (int)rows.size();
         J.max_radius = (max_radius && max_radius[j] >= 0) ? max_radius[j] : -1;
-        for (auto& r : rows) J.gsm.push_back(make_gensm(r.data(), n[j]));
+        J.gsm = make_gensms(rows, n[j]);
         std::vector<uint8_t> flat;
         for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
         J.order = rows.empty() ? 1 : cg::group_order(n[j], (int)rows.size(), flat.data());
