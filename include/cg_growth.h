@@ -182,6 +182,42 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
 /* Release the batch and its device buffers.  NULL is accepted. */
 int cg_batch_destroy(cg_batch_t b);
 
+/* ---- serving: continuous batching of growth jobs ---------------------------------------- */
+/*
+ * A request loop for many growth jobs of different n, generator sets and radius caps.  Jobs are
+ * queued by cg_server_submit (host only, no GPU work) and admitted into one of max_slots
+ * device slots, first come first served, while the sum of their predicted device memory stays
+ * within mem_budget.  The prediction bounds the states a job can reach by its radius cap
+ * (sphere r of an out-degree-k graph holds at most k (k-1)^(r-1) states when the set is
+ * inverse-closed, k^r otherwise, and never more than the group order), capped at job_mem_cap
+ * bytes per job (a job that needs more stops with CG_TRUNC_MEMCAP; its reported layers are
+ * exact).  Each cg_server_step admits what fits, then runs up to rounds_per_step layer steps of
+ * every admitted job in one persistent launch on the caller's stream (jobs' states stay on the
+ * device between steps), waits for it, and retires the jobs that ended, releasing their slot
+ * and memory.  Results are the same as cg_growth_run's for the same job with the same memory.
+ *   cg_server_create   mem_budget 0 = 160 GiB; job_mem_cap 0 = 2 GiB.  Errors: CG_EINVAL.
+ *   cg_server_submit   arguments as cg_growth_create; *job_id_out receives the job's id.
+ *                      Errors: CG_EINVAL (also more than 128 distinct generators), CG_ENOTCLOSED.
+ *   cg_server_step     *active_out: jobs admitted after the step; *finished_out: jobs that
+ *                      ended in this call.  Errors: CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT.
+ *   cg_server_finished pops up to cap ids of ended jobs (in ending order) into ids_out.
+ *   cg_server_result   copies an ended job's growth (its own return code in *status_out) and
+ *                      forgets it; CG_EINVAL with *num_layers_out = -1 if it has not ended, or
+ *                      with the needed size if cap is too small.
+ *   cg_server_load     jobs queued, jobs admitted, device bytes admitted jobs hold.
+ */
+typedef struct cg_server* cg_server_t;
+int cg_server_create(uint64_t mem_budget, int max_slots, uint64_t job_mem_cap, int rounds_per_step,
+                     cg_server_t* out);
+int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inverse_closed,
+                     int max_radius, uint64_t* job_id_out);
+int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finished_out);
+int cg_server_finished(cg_server_t s, uint64_t* ids_out, int cap, int* count_out);
+int cg_server_result(cg_server_t s, uint64_t job_id, uint64_t* layers_out, int cap,
+                     int* num_layers_out, int* status_out);
+int cg_server_load(cg_server_t s, int* queued, int* active, uint64_t* used_bytes);
+int cg_server_destroy(cg_server_t s);
+
 /* ---- growth without allocation ------------------------------------------------------- */
 /*
  * The paper has no counterpart to this entry point; it exists for callers that cannot allocate

@@ -65,6 +65,14 @@ SIGNATURES = {
                                        ctypes.POINTER(_vp)]),
     "cg_batch_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip, _ip]),
     "cg_batch_destroy": (ctypes.c_int, [_vp]),
+    "cg_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.POINTER(_vp)]),
+    "cg_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int, _u64p]),
+    "cg_server_step": (ctypes.c_int, [_vp, _vp, _ip, _ip]),
+    "cg_server_finished": (ctypes.c_int, [_vp, _u64p, ctypes.c_int, _ip]),
+    "cg_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _u64p, ctypes.c_int, _ip, _ip]),
+    "cg_server_load": (ctypes.c_int, [_vp, _ip, _ip, _u64p]),
+    "cg_server_destroy": (ctypes.c_int, [_vp]),
     "cg_growth_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int,
                                              _vp, _u64p, ctypes.c_int, _ip]),
     "cg_expand": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _vp, ctypes.c_uint64, _vp, _vp]),
@@ -126,6 +134,13 @@ cg_strerror = _export("cg_strerror")
 cg_batch_create = _export("cg_batch_create")
 cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")
+cg_server_create = _export("cg_server_create")
+cg_server_submit = _export("cg_server_submit")
+cg_server_step = _export("cg_server_step")
+cg_server_finished = _export("cg_server_finished")
+cg_server_result = _export("cg_server_result")
+cg_server_load = _export("cg_server_load")
+cg_server_destroy = _export("cg_server_destroy")
 cg_growth_run_noalloc = _export("cg_growth_run_noalloc")
 cg_expand = _export("cg_expand")
 cg_hash_insert = _export("cg_hash_insert")

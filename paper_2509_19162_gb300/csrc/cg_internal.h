@@ -36,6 +36,8 @@ enum JobStatus : int {
     kTruncAbove = 3,    // recorded the first layer larger than stop_above
     kNeedMem = 4,       // the layer being built did not fit; layers up to `radius` are exact
     kDeviceError = 5,
+    kFresh = 6,         // admitted, not yet initialised (the next init launch sets it up)
+    kEmptySlot = 7,     // no job in this slot
 };
 
 // One growth job of the hash strategy as the persistent kernel sees it.

@@ -11,8 +11,10 @@ namespace cg {
 // hash strategy (hash_path.cu)
 int hash_grow_block();
 int hash_grow_max_grid(int device, int ilp);
+// Initialise every job (only_fresh = 0) or only the jobs whose status is kFresh, then lay out
+// the first round's work over all running jobs.
 cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
-                             cudaStream_t st);
+                             cudaStream_t st, int only_fresh = 0);
 cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                                 cudaStream_t st);
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,

@@ -239,8 +239,13 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     u0 = ld_relaxed_ull(ubeg + j);
                 }
                 if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
-                do_unit<kProbeILP, kMode>(J, J->gens, lo + ((u - u0) << 5) + lane, hi, buf, cnt, lane,
-                                          overflow_seen);
+                // In the rank-bitmap variant a launch may mix jobs of both visited-set kinds.
+                if (kMode == kVisitBitmap && J->mode != kVisitBitmap)
+                    do_unit<kProbeILP, kVisitHash>(J, J->gens, lo + ((u - u0) << 5) + lane, hi, buf,
+                                                   cnt, lane, overflow_seen);
+                else
+                    do_unit<kProbeILP, kMode>(J, J->gens, lo + ((u - u0) << 5) + lane, hi, buf, cnt,
+                                              lane, overflow_seen);
             }
             if (J) stage_flush(buf, cnt, J, lane);
         }
@@ -256,10 +261,11 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
 }
 
 // Set up job j for a run from the identity: the table must already be cleared.
-__global__ void init_jobs_kernel(JobDev* jobs, int njobs) {
+__global__ void init_jobs_kernel(JobDev* jobs, int njobs, int only_fresh) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= njobs) return;
     JobDev& J = jobs[j];
+    if (only_fresh && J.status != kFresh) return;
     uint64_t id = 0;
     for (int i = 0; i < J.n; ++i) id |= (uint64_t)i << (4 * i);
     J.keys[0] = id;
@@ -391,8 +397,8 @@ int hash_grow_max_grid(int device, int ilp) {
 }
 
 cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
-                             cudaStream_t st) {
-    init_jobs_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs);
+                             cudaStream_t st, int only_fresh) {
+    init_jobs_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs, only_fresh);
     init_units_kernel<<<1, 1, 0, st>>>(d_jobs, njobs, d_ubeg, d_ctl);
     return cudaGetLastError();
 }

@@ -852,10 +852,10 @@ struct cg_batch {
         std::vector<GenSM> gsm;
         uint64_t order = 1;
         uint64_t cap = 1;          // states the job may store
+        int mode = cg::kVisitHash; // rank bitmap for small dense groups, else hash table
     };
     std::vector<Job> jobs;
     uint64_t mem_cap = kDefaultMemCap;
-    int mode = cg::kVisitHash;     // one visited-set kind for the whole batch
 };
 
 namespace {
@@ -873,12 +873,11 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     auto al = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
     uint64_t ngens = 0, nkeys = 0, nslots = 0;
     std::vector<uint64_t> goff(nj), koff(nj), toff(nj), slots(nj);
-    const bool bitmap = b->mode == cg::kVisitBitmap;
     for (int i = 0; i < nj; ++i) {
         const auto& J = b->jobs[ids[i]];
         goff[i] = ngens; ngens += J.gsm.size();
         koff[i] = nkeys; nkeys += J.cap;
-        slots[i] = bitmap ? bitmap_words(J.n) / 2 : table_slots_for(J.cap);
+        slots[i] = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) / 2 : table_slots_for(J.cap);
         toff[i] = nslots; nslots += slots[i];
     }
     const int lcap = cap + 1;
@@ -911,8 +910,8 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
         D.n = J.n;
         D.layers_cap = lcap;
         D.max_radius = J.max_radius;
-        D.mode = b->mode;
-        D.bitmap_words = bitmap ? bitmap_words(J.n) : 0;
+        D.mode = J.mode;
+        D.bitmap_words = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) : 0;
     }
     JobDev* d_jobs = (JobDev*)(base + o_jobs);
     unsigned long long* d_ubeg = (unsigned long long*)(base + o_ubeg);
@@ -920,7 +919,16 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     cudaError_t e = cudaSuccess;
     if (ngens) e = cudaMemcpyAsync(base + o_gens, hg.data(), ngens * sizeof(GenSM), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, hj.data(), nj * sizeof(JobDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tab, bitmap ? 0 : 0xFF, nslots * 8, st);
+    // visited sets: bitmaps start all-zero, hash tables all-ones (empty marker); runs of jobs of
+    // one kind are filled with one memset each
+    for (int i = 0; i < nj && e == cudaSuccess;) {
+        const int mode = b->jobs[ids[i]].mode;
+        int j = i;
+        uint64_t cnt = 0;
+        while (j < nj && b->jobs[ids[j]].mode == mode) cnt += slots[j++];
+        e = cudaMemsetAsync(base + o_tab + toff[i] * 8, mode == cg::kVisitBitmap ? 0 : 0xFF, cnt * 8, st);
+        i = j;
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
     if (e == cudaSuccess)
@@ -994,13 +1002,15 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_rc(e);
     int maxk = 1;
-    bool all_bitmap = true;
+    bool any_bitmap = false;
     for (auto& J : b->jobs) {
         maxk = std::max(maxk, J.k);
-        all_bitmap &= (J.k == 0 || (J.n <= 12 && bitmap_eligible(J.n, J.order, b->mem_cap)));
+        J.mode = (J.k > 0 && J.n <= 12 && bitmap_eligible(J.n, J.order, b->mem_cap)) ? cg::kVisitBitmap
+                                                                                     : cg::kVisitHash;
+        any_bitmap |= J.mode == cg::kVisitBitmap;
     }
-    b->mode = all_bitmap ? cg::kVisitBitmap : cg::kVisitHash;
-    const int ilp = default_ilp(maxk) + (all_bitmap ? 16 : 0);
+    // The rank-bitmap kernel variant also runs hash-table jobs of the same launch.
+    const int ilp = default_ilp(maxk) + (any_bitmap ? 16 : 0);
     const int grid = grow_grid(dev, ilp);
     if (grid <= 0) return CG_ECUDA;
     const uint64_t budget = b->mem_cap;
@@ -1024,7 +1034,7 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
             continue;
         }
         J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
-        const uint64_t vis = b->mode == cg::kVisitBitmap ? J.cap * 8 + bitmap_words(J.n) * 4 : bytes_for(J.cap);
+        const uint64_t vis = J.mode == cg::kVisitBitmap ? J.cap * 8 + bitmap_words(J.n) * 4 : bytes_for(J.cap);
         const uint64_t need = vis + sizeof(GenSM) * J.gsm.size() + sizeof(JobDev) +
                               (uint64_t)(cap + 1) * 8 + 1024;
         if (!wave.empty() && wave_bytes + need > budget) flush();
@@ -1037,6 +1047,335 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
 
 int cg_batch_destroy(cg_batch_t b) {
     delete b;
+    return CG_OK;
+}
+
+}  // extern "C"
+
+// ---- serving: continuous batching of growth jobs ------------------------------------------------
+// Jobs are queued on the host, admitted into device slots while their predicted memory fits the
+// budget, and every cg_server_step runs up to `rounds_per_step` layer steps of every admitted
+// job in one persistent launch.  A job's states and visited set stay on the device between
+// steps; finished jobs release their slot and memory at the end of the step in which they end,
+// and queued jobs take their place at the start of the next step.
+#include <deque>
+#include <unordered_map>
+
+namespace {
+
+constexpr int kSrvMaxGens = 128;     // generators per job
+constexpr int kSrvLayers = 4096;     // layer sizes kept per job (more: CG_TRUNC_RADIUS)
+
+// Upper bound on the states a job visits up to its radius cap: sphere r of a graph of
+// out-degree k has at most k (k-1)^(r-1) elements when the set is inverse-closed (no walk
+// returns along the edge it came by), k^r otherwise; never more than the group order.
+uint64_t predict_states(int k, uint64_t order, int max_radius, bool inverse_closed) {
+    if (max_radius < 0) return order;
+    uint64_t total = 1, layer = 1;
+    for (int r = 1; r <= max_radius; ++r) {
+        const uint64_t f = (r == 1 || !inverse_closed) ? (uint64_t)k : (uint64_t)(k > 1 ? k - 1 : 1);
+        layer = (layer > order / std::max<uint64_t>(f, 1)) ? order : layer * f;
+        total += std::min(layer, order);
+        if (total >= order) return order;
+    }
+    return std::min(total, order);
+}
+
+}  // namespace
+
+struct cg_server {
+    struct Job {
+        uint64_t id = 0;
+        int n = 0, k = 0, max_radius = -1;
+        std::vector<GenSM> gsm;
+        uint64_t order = 1, cap = 1, bytes = 0, visited_words = 0;
+        int mode = cg::kVisitHash;
+    };
+    struct Slot {
+        bool used = false;
+        Job job;
+        char* mem = nullptr;
+    };
+    struct Result {
+        std::vector<uint64_t> layers;
+        int status = 0;
+    };
+    uint64_t budget = 0, used = 0, job_cap_bytes = 0;
+    int max_slots = 0, rounds_per_step = 8, active = 0, device = -1;
+    std::deque<Job> queue;
+    std::vector<Slot> slots;
+    std::vector<JobDev> h_jobs;
+    std::unordered_map<uint64_t, Result> results;
+    std::vector<uint64_t> finished;
+    uint64_t next_id = 1;
+    JobDev* d_jobs = nullptr;
+    unsigned long long* d_ubeg = nullptr;
+    Ctl* d_ctl = nullptr;
+    GenSM* d_gens = nullptr;
+    uint64_t* d_layers = nullptr;
+};
+
+namespace {
+
+int server_init_device(cg_server* s, cudaStream_t st) {
+    if (s->d_jobs) return CG_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_rc(e);
+    s->device = dev;
+    const int m = s->max_slots;
+    s->d_jobs = (JobDev*)dev_alloc(sizeof(JobDev) * m, st);
+    s->d_ubeg = (unsigned long long*)dev_alloc(8 * (m + 1), st);
+    s->d_ctl = (Ctl*)dev_alloc(sizeof(Ctl), st);
+    s->d_gens = (GenSM*)dev_alloc(sizeof(GenSM) * kSrvMaxGens * m, st);
+    s->d_layers = (uint64_t*)dev_alloc(8ull * kSrvLayers * m, st);
+    if (!s->d_jobs || !s->d_ubeg || !s->d_ctl || !s->d_gens || !s->d_layers) return CG_ENOMEM;
+    s->h_jobs.assign(m, JobDev{});
+    for (auto& J : s->h_jobs) {
+        std::memset(&J, 0, sizeof(J));
+        J.status = cg::kEmptySlot;
+    }
+    if ((e = cudaMemcpyAsync(s->d_jobs, s->h_jobs.data(), sizeof(JobDev) * m, cudaMemcpyHostToDevice, st)))
+        return cuda_rc(e);
+    return CG_OK;
+}
+
+// Move queued jobs into free slots while the budget allows (first come, first served).
+int server_admit(cg_server* s, cudaStream_t st) {
+    while (!s->queue.empty()) {
+        int free_slot = -1;
+        for (int i = 0; i < s->max_slots; ++i)
+            if (!s->slots[i].used) { free_slot = i; break; }
+        if (free_slot < 0) break;
+        cg_server::Job& q = s->queue.front();
+        if (s->used + q.bytes > s->budget && s->active > 0) break;
+        char* mem = (char*)dev_alloc(q.bytes, st);
+        if (!mem) {
+            if (s->active > 0) break;    // wait for memory to free up
+            return CG_ENOMEM;
+        }
+        cg_server::Slot& sl = s->slots[free_slot];
+        sl.used = true;
+        sl.job = q;
+        sl.mem = mem;
+        s->queue.pop_front();
+        s->used += sl.job.bytes;
+        s->active += 1;
+        const cg_server::Job& J = sl.job;
+        JobDev D;
+        std::memset(&D, 0, sizeof(D));
+        D.keys = reinterpret_cast<uint64_t*>(mem);
+        D.keys_cap = J.cap;
+        D.table = reinterpret_cast<uint64_t*>(mem + J.cap * 8);
+        D.table_mask = J.mode == cg::kVisitBitmap ? 0 : J.visited_words - 1;
+        D.gens = s->d_gens + (size_t)free_slot * kSrvMaxGens;
+        D.layer_sizes = s->d_layers + (size_t)free_slot * kSrvLayers;
+        D.k = J.k;
+        D.n = J.n;
+        D.layers_cap = kSrvLayers;
+        D.max_radius = J.max_radius;
+        D.mode = J.mode;
+        D.bitmap_words = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) : 0;
+        D.status = cg::kFresh;
+        s->h_jobs[free_slot] = D;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync((void*)D.gens, J.gsm.data(), sizeof(GenSM) * J.k, cudaMemcpyHostToDevice, st)))
+            return cuda_rc(e);
+        if ((e = cudaMemsetAsync(D.table, J.mode == cg::kVisitBitmap ? 0 : 0xFF, J.visited_words * 8, st)))
+            return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(s->d_jobs + free_slot, &s->h_jobs[free_slot], sizeof(JobDev),
+                                 cudaMemcpyHostToDevice, st)))
+            return cuda_rc(e);
+    }
+    return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_server_create(uint64_t mem_budget, int max_slots, uint64_t job_mem_cap, int rounds_per_step,
+                     cg_server_t* out) {
+    if (!out || max_slots < 1 || max_slots > 4096 || rounds_per_step < 1) return CG_EINVAL;
+    *out = nullptr;
+    cg_server* s = new (std::nothrow) cg_server();
+    if (!s) return CG_ENOMEM;
+    s->budget = mem_budget ? mem_budget : kDefaultMemCap;
+    s->job_cap_bytes = job_mem_cap ? job_mem_cap : (2ull << 30);
+    s->max_slots = max_slots;
+    s->rounds_per_step = rounds_per_step;
+    s->slots.resize(max_slots);
+    *out = s;
+    return CG_OK;
+}
+
+int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inverse_closed,
+                     int max_radius, uint64_t* job_id_out) {
+    if (!s || !job_id_out) return CG_EINVAL;
+    int rc = validate(n, k, gens);
+    if (rc) return rc;
+    auto rows = clean_rows(n, k, gens);
+    if (inverse_closed && !closed_under_inverse(rows, n)) return CG_ENOTCLOSED;
+    if ((int)rows.size() > kSrvMaxGens) return CG_EINVAL;
+    cg_server::Job J;
+    J.id = s->next_id++;
+    J.n = n;
+    J.k = (int)rows.size();
+    J.max_radius = max_radius < 0 ? -1 : max_radius;
+    J.gsm = make_gensms(rows, n);
+    std::vector<uint8_t> flat;
+    for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
+    J.order = rows.empty() ? 1 : cg::group_order(n, (int)rows.size(), flat.data());
+    // predicted memory: states up to the radius cap, within the per-job cap
+    const uint64_t want = std::max<uint64_t>(1, predict_states(std::max(J.k, 1), J.order, J.max_radius,
+                                                               inverse_closed != 0));
+    const bool bm_ok = n <= 12 && n >= 2;
+    const uint64_t bm_bytes = bm_ok ? bitmap_words(n) * 4 : ~0ull;
+    uint64_t cap = want;
+    uint64_t hash_bytes = cap * 8 + table_slots_for(cap) * 8;
+    if (hash_bytes > s->job_cap_bytes) {
+        cap = std::max<uint64_t>(1, max_cap_for_mem(s->job_cap_bytes));
+        hash_bytes = cap * 8 + table_slots_for(cap) * 8;
+    }
+    if (bm_ok && cap * 8 + bm_bytes <= hash_bytes) {
+        J.mode = cg::kVisitBitmap;
+        J.visited_words = bm_bytes / 8;
+    } else {
+        J.mode = cg::kVisitHash;
+        J.visited_words = table_slots_for(cap);
+    }
+    J.cap = cap;
+    J.bytes = ((cap * 8 + 255) & ~255ull) + J.visited_words * 8;
+    if (J.k == 0 || J.max_radius == 0) {       // only the identity: done at once
+        cg_server::Result R;
+        R.layers = {1};
+        R.status = J.k == 0 ? CG_OK : CG_TRUNC_RADIUS;
+        s->results[J.id] = R;
+        s->finished.push_back(J.id);
+    } else {
+        s->queue.push_back(std::move(J));
+    }
+    *job_id_out = s->next_id - 1;
+    return CG_OK;
+}
+
+int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finished_out) {
+    if (!s) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = server_init_device(s, st);
+    if (rc) return rc;
+    const size_t finished_before = s->finished.size();
+    if ((rc = server_admit(s, st))) return rc;
+    if (s->active > 0) {
+        int maxk = 1;
+        bool any_bitmap = false;
+        for (auto& sl : s->slots)
+            if (sl.used) {
+                maxk = std::max(maxk, sl.job.k);
+                any_bitmap |= sl.job.mode == cg::kVisitBitmap;
+            }
+        const int variant = default_ilp(maxk) + (any_bitmap ? 16 : 0);
+        const int grid = grow_grid(s->device, variant);
+        if (grid <= 0) return CG_ECUDA;
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(s->d_ctl, 0, sizeof(Ctl), st))) return cuda_rc(e);
+        if ((e = cg::launch_init_jobs(s->d_jobs, s->max_slots, s->d_ubeg, s->d_ctl, st, 1))) return cuda_rc(e);
+        if ((e = cg::launch_hash_grow(s->d_jobs, s->max_slots, s->d_ubeg, s->d_ctl, grid,
+                                      s->rounds_per_step, kTimeoutNs, variant, st)))
+            return cuda_rc(e);
+        Ctl ctl;
+        if ((e = cudaMemcpyAsync(s->h_jobs.data(), s->d_jobs, sizeof(JobDev) * s->max_slots,
+                                 cudaMemcpyDeviceToHost, st)))
+            return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(&ctl, s->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st))) return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st))) return cuda_rc(e);
+        if (ctl.err) return ctl.err;
+        // retire the jobs that ended in this step
+        std::vector<int> ended;
+        for (int i = 0; i < s->max_slots; ++i) {
+            if (!s->slots[i].used) continue;
+            const int stt = s->h_jobs[i].status;
+            if (stt != cg::kRunning && stt != cg::kFresh) ended.push_back(i);
+        }
+        std::vector<std::vector<uint64_t>> lay(ended.size());
+        for (size_t q = 0; q < ended.size(); ++q) {
+            const int i = ended[q];
+            lay[q].resize(s->h_jobs[i].radius + 1);
+            if ((e = cudaMemcpyAsync(lay[q].data(), s->d_layers + (size_t)i * kSrvLayers,
+                                     8 * lay[q].size(), cudaMemcpyDeviceToHost, st)))
+                return cuda_rc(e);
+        }
+        if (!ended.empty() && (e = cudaStreamSynchronize(st))) return cuda_rc(e);
+        for (size_t q = 0; q < ended.size(); ++q) {
+            const int i = ended[q];
+            cg_server::Slot& sl = s->slots[i];
+            cg_server::Result R;
+            R.layers = std::move(lay[q]);
+            R.status = status_to_rc(s->h_jobs[i].status);
+            s->results[sl.job.id] = std::move(R);
+            s->finished.push_back(sl.job.id);
+            dev_free(sl.mem, st);
+            sl.mem = nullptr;
+            sl.used = false;
+            s->used -= sl.job.bytes;
+            s->active -= 1;
+            s->h_jobs[i].status = cg::kEmptySlot;
+            if ((e = cudaMemcpyAsync(s->d_jobs + i, &s->h_jobs[i], sizeof(JobDev), cudaMemcpyHostToDevice, st)))
+                return cuda_rc(e);
+        }
+        if (!ended.empty() && (e = cudaStreamSynchronize(st))) return cuda_rc(e);
+    }
+    if (active_out) *active_out = s->active;
+    if (finished_out) *finished_out = (int)(s->finished.size() - finished_before);
+    return CG_OK;
+}
+
+int cg_server_finished(cg_server_t s, uint64_t* ids_out, int cap, int* count_out) {
+    if (!s || !count_out || cap < 0) return CG_EINVAL;
+    const int n = (int)std::min<size_t>(s->finished.size(), (size_t)cap);
+    for (int i = 0; i < n; ++i) ids_out[i] = s->finished[i];
+    s->finished.erase(s->finished.begin(), s->finished.begin() + n);
+    *count_out = n;
+    return CG_OK;
+}
+
+int cg_server_result(cg_server_t s, uint64_t job_id, uint64_t* layers_out, int cap,
+                     int* num_layers_out, int* status_out) {
+    if (!s || !num_layers_out || !status_out) return CG_EINVAL;
+    auto it = s->results.find(job_id);
+    if (it == s->results.end()) {
+        *num_layers_out = -1;
+        return CG_EINVAL;
+    }
+    const int nl = (int)it->second.layers.size();
+    *num_layers_out = nl;
+    *status_out = it->second.status;
+    if (cap < nl || !layers_out) return CG_EINVAL;
+    for (int r = 0; r < nl; ++r) layers_out[r] = it->second.layers[r];
+    s->results.erase(it);
+    return CG_OK;
+}
+
+int cg_server_load(cg_server_t s, int* queued, int* active, uint64_t* used_bytes) {
+    if (!s) return CG_EINVAL;
+    if (queued) *queued = (int)s->queue.size();
+    if (active) *active = s->active;
+    if (used_bytes) *used_bytes = s->used;
+    return CG_OK;
+}
+
+int cg_server_destroy(cg_server_t s) {
+    if (!s) return CG_OK;
+    if (s->device >= 0) {
+        for (auto& sl : s->slots) dev_free(sl.mem, nullptr);
+        dev_free(s->d_jobs, nullptr);
+        dev_free(s->d_ubeg, nullptr);
+        dev_free(s->d_ctl, nullptr);
+        dev_free(s->d_gens, nullptr);
+        dev_free(s->d_layers, nullptr);
+        cudaStreamSynchronize(nullptr);
+    }
+    delete s;
     return CG_OK;
 }
 

@@ -111,3 +111,22 @@ def test_batch_create_validation(lib):
     b.close()
     with pytest.raises(RuntimeError):
         Batch([(5, w.lx(5), True, -1)])
+
+
+def test_server_host_logic(lib):
+    from paper_2509_19162_gb300.serve import Server
+    with Server(mem_budget=1 << 30, max_slots=4) as s:
+        with pytest.raises(RuntimeError):
+            s.submit(5, [[0, 0, 1, 2, 3]])                      # not a permutation
+        with pytest.raises(RuntimeError):
+            s.submit(5, w.lx(5), inverse_closed=True)          # not inverse-closed
+        a = s.submit(4, [[0, 1, 2, 3]])                        # identity only: ends at once
+        b = s.submit(6, w.coxeter(6), max_radius=0)            # radius 0: ends at once
+        c = s.submit(6, w.coxeter(6))                          # queued
+        assert s.load()[0] == 1
+        assert sorted(s.finished()) == sorted([a, b])
+        r = s.result(a)
+        assert r.layers == [1] and r.status == 0
+        assert s.result(b).status == 1
+        with pytest.raises(RuntimeError):
+            s.result(c)                                        # not run yet
