@@ -325,19 +325,191 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------------------------
+# Config 4: 4096 independent random groups, one persistent launch per batch run
+
+def run_batch(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2509_19162_gb300 as cg
+    cg.build()
+    jobs_all = wl.batch_groups()
+    jobs = jobs_all[rank::world]                  # the groups shard across ranks, no exchange
+    spec = [(j.n, j.gens, j.inverse_closed, -1) for j in jobs]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    batch = cg.Batch(spec)
+    res = None
+    for _ in range(args.warmup):
+        res = batch.run(stream)
+    layers = [r.layers for r in res]
+    nb_step = sum(len(j.gens) * sum(l) for j, l in zip(jobs, layers))
+    bytes_step = sum(algorithmic_bytes(l, len(j.gens), True) for j, l in zip(jobs, layers))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    total_ms, kernel_ms, launches = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = batch.run(stream)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        st = batch.stats()
+        kernel_ms += st["kernel_ms"]
+        launches += st["launches"]
+        if [r.layers for r in out] != layers:
+            raise RuntimeError("batched layer counts changed between steps")
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    variant = batch.stats()["probe_variant"]
+    batch.close()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        n_all = torch.tensor([nb_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(n_all)
+        nb_all = float(n_all.item())
+    else:
+        nb_all = nb_step
+    value = nb_all * args.steps / (total_ms / 1000.0)
+    jobs_per_s = len(jobs_all) * args.steps / (total_ms / 1000.0)
+    # end to end: create + run + destroy from host inputs
+    t0 = time.perf_counter()
+    with cg.Batch(spec) as b2:
+        b2.run(stream)
+        est = b2.stats()
+    e2e_s = time.perf_counter() - t0
+    # one at a time, same GPU, first 512 groups of this rank's share (same results required)
+    sample = jobs[:512]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = [cg.growth(j.n, j.gens, j.inverse_closed, stream=stream).layers for j in sample]
+    one_s = time.perf_counter() - t0
+    if single != layers[:len(sample)]:
+        raise RuntimeError("one-at-a-time results differ from the batched results")
+    peak, peak_kind = load_peaks()
+    kms = kernel_ms / args.steps
+    achieved = bytes_step / (kms / 1000.0) / 1e9
+    if rank != 0:
+        return 0
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}",
+                   "groups": len(jobs_all), "states": sum(sum(l) for l in layers),
+                   "neighbours_per_step": nb_step, "jobs_per_s": jobs_per_s,
+                   "one_at_a_time_jobs_per_s": len(sample) / one_s,
+                   "batched_over_one_at_a_time": jobs_per_s / (len(sample) / one_s),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "groups sharded over ranks" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}> (multi-job)",
+                     "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind},
+        "e2e": {"value": nb_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": est["h2d_bytes"],
+                "d2h_bytes_per_step": est["d2h_bytes"], "api": "paper_2509_19162_gb300.Batch(...).run()"},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# --------------------------------------------------------------------------------------------
+# Config 5: Poisson stream of growth jobs through the continuous-batching server
+
+def run_serve(args):
+    import torch
+    import numpy as np
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2509_19162_gb300 as cg
+    from paper_2509_19162_gb300.serve import Server, serve_stream
+    cg.build()
+    jobs = wl.serve_stream(count=args.serve_jobs)
+    stream = torch.cuda.Stream()
+    budget = 160 << 30
+    job_cap = args.serve_job_mem << 20
+    # one at a time on the same GPU (each job alone, same per-job memory cap): capacity lambda_1
+    sample = jobs[:200]
+    for j in sample[:20]:
+        cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=job_cap, stream=stream)
+    t0 = time.perf_counter()
+    for j in sample:
+        cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=job_cap, stream=stream)
+    lam1 = len(sample) / (time.perf_counter() - t0)
+    lines = []
+    for mult in (1.0, 2.0):
+        lam = lam1 * mult
+        arr = [j.arrival / lam for j in jobs]
+        with Server(mem_budget=budget, max_slots=args.serve_slots, job_mem_cap=job_cap,
+                    rounds_per_step=args.serve_rounds) as srv:
+            sampler = ClockSampler(0)
+            sampler.start()
+            rep = serve_stream(jobs, arr, srv, stream)
+            clocks = sampler.stop()
+        statuses = [r.status for r in rep.results]
+        lines.append({
+            "metric": "jobs/sec + p50/p99 latency (serving)", "value": rep.jobs_per_s, "unit": "jobs/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": rep.makespan_s * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"serving-{len(jobs)}-jobs-seed{wl.SERVE_SEED}", "arrival_rate_jobs_per_s": lam,
+                       "rate": f"{mult:g} x one-at-a-time capacity ({lam1:.1f} jobs/s)",
+                       "mem_budget_gib": budget >> 30, "job_mem_cap_mib": args.serve_job_mem,
+                       "slots": args.serve_slots, "rounds_per_step": args.serve_rounds,
+                       "server_steps": rep.steps, "max_active": rep.max_active,
+                       "mean_active": rep.mean_active,
+                       "ended": {"complete": statuses.count(0), "radius_cap": statuses.count(1),
+                                 "mem_cap": statuses.count(2)}},
+            "latency_ms": {"p50": rep.percentile_ms(50), "p99": rep.percentile_ms(99),
+                           "mean": float(np.mean(rep.latency_s) * 1000.0)},
+            "one_at_a_time_jobs_per_s": lam1,
+            "clocks": clocks,
+        })
+    for ln in lines:
+        print(json.dumps(ln))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="s11_lrx", choices=["s11_lrx", "s8_coxeter", "s14_pancake"])
+    ap.add_argument("--workload", default="s11_lrx",
+                    choices=["s11_lrx", "s8_coxeter", "s14_pancake", "batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=20000)
+    ap.add_argument("--serve-job-mem", type=int, default=64, help="per-job device memory cap, MiB")
+    ap.add_argument("--serve-slots", type=int, default=512)
+    ap.add_argument("--serve-rounds", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
+        if args.workload in ("batch", "serve"):
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm covers the single-growth workloads"}))
+            return 0
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -179,6 +179,9 @@ int cg_batch_create(int njobs, const int* n, const int* k, const uint8_t* gens,
 int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int cap,
                  int* num_layers_out, int* status_out);
 
+/* Measurements of the last cg_batch_run (as cg_growth_get_stats).  Errors: CG_EINVAL. */
+int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out);
+
 /* Release the batch and its device buffers.  NULL is accepted. */
 int cg_batch_destroy(cg_batch_t b);
 

@@ -194,6 +194,11 @@ class Batch:
                                       ctypes.byref(h)), "cg_batch_create")
         self._h = h
 
+    def stats(self) -> dict:
+        st = _cg.cg_growth_stats()
+        _cg.check(_cg.cg_batch_get_stats(self._h, ctypes.byref(st)), "cg_batch_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
     def run(self, stream=None, cap: int = 512) -> List[GrowthResult]:
         out = np.zeros(self.njobs * cap, dtype=np.uint64)
         nl = np.zeros(self.njobs, dtype=np.int32)

@@ -232,16 +232,16 @@ __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
     return r;
 }
 
-// Visited test-and-set of G keys in a rank-indexed bitmap (one bit per element of S_n).  A
-// plain L2 load first, so that keys already visited cost no atomic; then atomicOr decides the
-// race between equal keys.  res[i] = 1 if this call set the bit, 0 if it was set, -1 if the
-// rank fell outside the bitmap (not a permutation of 0..n-1).
+// Visited test-and-set of G keys in a rank-indexed bitmap (one bit per element of S_n): one
+// atomicOr per key, whose returned word says whether the bit was already set (a single L2
+// round trip whether the key is new or not).  res[i] = 1 if this call set the bit, 0 if it
+// was set, -1 if the rank fell outside the bitmap (not a permutation of 0..n-1).
 template <int G>
 __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words, int n,
                                                     const uint64_t (&key)[G], int (&res)[G],
                                                     unsigned vmask) {
     uint64_t w[G];
-    unsigned bit[G], v[G];
+    unsigned bit[G], old[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         res[i] = 0;
@@ -252,14 +252,10 @@ __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words
     }
 #pragma unroll
     for (int i = 0; i < G; ++i)
-        if ((vmask >> i & 1u) && res[i] == 0) v[i] = __ldcg(bm + w[i]);
+        if ((vmask >> i & 1u) && res[i] == 0) old[i] = atomicOr(bm + w[i], bit[i]);
 #pragma unroll
-    for (int i = 0; i < G; ++i) {
-        if ((vmask >> i & 1u) && res[i] == 0 && !(v[i] & bit[i])) {
-            const unsigned old = atomicOr(bm + w[i], bit[i]);
-            res[i] = (old & bit[i]) ? 0 : 1;
-        }
-    }
+    for (int i = 0; i < G; ++i)
+        if ((vmask >> i & 1u) && res[i] == 0) res[i] = (old[i] & bit[i]) ? 0 : 1;
 }
 
 // Arrival half of a grid barrier whose last arriving block does some work before releasing

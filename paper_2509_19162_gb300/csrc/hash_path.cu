@@ -136,10 +136,9 @@ __device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, 
 template <int kProbeILP, int kMode>
 __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned long long idx,
                                         unsigned long long hi, uint64_t* buf, int& cnt, int lane,
-                                        bool& overflow_seen) {
+                                        bool& overflow_seen, uint64_t s) {
     const bool active = idx < hi;
     const int n = J->n;
-    uint64_t s = active ? __ldcg(J->keys + idx) : 0;
     unsigned tag = 0;                       // 1 + generator that leads back to the parent
     if (n <= 15) {
         tag = (unsigned)(s >> 60);
@@ -215,8 +214,15 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
             const unsigned long long lo = ld_relaxed_ull(&J->lo);
             const unsigned long long hi = ld_relaxed_ull(&J->hi);
             unsigned iter = 0;
+            // The next unit's frontier key is loaded while the current unit is processed.
+            uint64_t s_next = 0;
+            if (warp0 < total && lo + (warp0 << 5) + lane < hi) s_next = __ldcg(J->keys + lo + (warp0 << 5) + lane);
             for (unsigned long long b = warp0; b < total; b += nwarps) {
-                do_unit<kProbeILP, kMode>(J, single_gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen);
+                const uint64_t s_cur = s_next;
+                const unsigned long long nb = b + nwarps;
+                s_next = (nb < total && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
+                do_unit<kProbeILP, kMode>(J, single_gens, lo + (b << 5) + lane, hi, buf, cnt, lane,
+                                          overflow_seen, s_cur);
                 // Stop early once any warp found the job's buffers full (the layer will be
                 // redone after the host grows them).
                 if ((++iter & 15u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
@@ -239,13 +245,13 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     u0 = ld_relaxed_ull(ubeg + j);
                 }
                 if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
+                const unsigned long long idx = lo + ((u - u0) << 5) + lane;
+                const uint64_t s0 = idx < hi ? __ldcg(J->keys + idx) : 0;
                 // In the rank-bitmap variant a launch may mix jobs of both visited-set kinds.
                 if (kMode == kVisitBitmap && J->mode != kVisitBitmap)
-                    do_unit<kProbeILP, kVisitHash>(J, J->gens, lo + ((u - u0) << 5) + lane, hi, buf,
-                                                   cnt, lane, overflow_seen);
+                    do_unit<kProbeILP, kVisitHash>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
                 else
-                    do_unit<kProbeILP, kMode>(J, J->gens, lo + ((u - u0) << 5) + lane, hi, buf, cnt,
-                                              lane, overflow_seen);
+                    do_unit<kProbeILP, kMode>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
             }
             if (J) stage_flush(buf, cnt, J, lane);
         }

@@ -232,8 +232,10 @@ int grow_grid(int dev, int ilp) {
     return device_grid_cache[dev][ilp];
 }
 
-// Generators probed together per thread: all of them when k <= 4, else 4.
-int default_ilp(int k) { return std::max(1, std::min(4, k)); }
+// Generators probed together per thread.  Hash tables (random DRAM probes): all of them when
+// k <= 4, else 4.  Rank bitmap (L2-resident, one atomic per probe): 1 -- measured fastest, and
+// the only bitmap variant that fits 64 registers without spilling.
+int default_ilp(int k, bool bitmap = false) { return bitmap ? 1 : std::max(1, std::min(4, k)); }
 
 }  // namespace
 
@@ -401,7 +403,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         rc = resize_state(h, std::max<uint64_t>(start, 1), 0, st);
         if (rc) return rc;
     }
-    const int ilp = (h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k)) + (bitmap ? 16 : 0);
+    const int ilp = (h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k, bitmap)) + (bitmap ? 16 : 0);
     const int grid_max = grow_grid(h->device, ilp);
     if (grid_max <= 0) return CG_ECUDA;
     // Small groups finish faster with fewer blocks at each barrier.
@@ -856,6 +858,8 @@ struct cg_batch {
     };
     std::vector<Job> jobs;
     uint64_t mem_cap = kDefaultMemCap;
+    cg_growth_stats stats{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
@@ -931,8 +935,15 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
+    if (e == cudaSuccess && !b->ev0) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess && !b->ev1) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev0, st);
     if (e == cudaSuccess)
         e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, grid, lcap + 1, kTimeoutNs, ilp, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev1, st);
+    b->stats.launches += 3;
+    b->stats.h2d_bytes += ngens * sizeof(GenSM) + nj * sizeof(JobDev);
+    b->stats.d2h_bytes += nj * sizeof(JobDev) + sizeof(Ctl) + (uint64_t)nj * lcap * 8;
     Ctl ctl;
     std::memset(&ctl, 0, sizeof(ctl));
     std::vector<uint64_t> lay((uint64_t)nj * lcap);
@@ -940,6 +951,9 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(lay.data(), base + o_lay, lay.size() * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess && cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats.kernel_ms += ms;
+    b->stats.rounds += ctl.rounds;
     if (e != cudaSuccess) rc = cuda_rc(e);
     else if (ctl.err) rc = ctl.err;
     if (rc == CG_OK) {
@@ -998,6 +1012,7 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
                  int* num_layers_out, int* status_out) {
     if (!b || !num_layers_out || cap < 1 || (!layer_sizes_out && !b->jobs.empty())) return CG_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::memset(&b->stats, 0, sizeof(b->stats));
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_rc(e);
@@ -1010,7 +1025,9 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
         any_bitmap |= J.mode == cg::kVisitBitmap;
     }
     // The rank-bitmap kernel variant also runs hash-table jobs of the same launch.
-    const int ilp = default_ilp(maxk) + (any_bitmap ? 16 : 0);
+    const int ilp = default_ilp(maxk, any_bitmap) + (any_bitmap ? 16 : 0);
+    b->stats.strategy_used = any_bitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
+    b->stats.probe_variant = ilp;
     const int grid = grow_grid(dev, ilp);
     if (grid <= 0) return CG_ECUDA;
     const uint64_t budget = b->mem_cap;
@@ -1045,7 +1062,15 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     return rc;
 }
 
+int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out) {
+    if (!b || !out) return CG_EINVAL;
+    *out = b->stats;
+    return CG_OK;
+}
+
 int cg_batch_destroy(cg_batch_t b) {
+    if (b && b->ev0) cudaEventDestroy(b->ev0);
+    if (b && b->ev1) cudaEventDestroy(b->ev1);
     delete b;
     return CG_OK;
 }
@@ -1274,7 +1299,7 @@ int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finis
                 maxk = std::max(maxk, sl.job.k);
                 any_bitmap |= sl.job.mode == cg::kVisitBitmap;
             }
-        const int variant = default_ilp(maxk) + (any_bitmap ? 16 : 0);
+        const int variant = default_ilp(maxk, any_bitmap) + (any_bitmap ? 16 : 0);
         const int grid = grow_grid(s->device, variant);
         if (grid <= 0) return CG_ECUDA;
         cudaError_t e;
