@@ -47,6 +47,24 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(kernel_name):
+    """DRAM bytes per launch of `kernel_name` from the committed ncu record (profiles/traffic.json),
+    or None when there is none or the kernel's sources changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel_name)
+        if not rec:
+            return None
+        h = hashlib.sha256()
+        for src in rec["kernel_sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["kernel_sources_sha256"] else None
+    except Exception:
+        return None
+
+
 def algorithmic_bytes(layers, k, complete):
     """Bytes the layer steps must move (per-step model B_r): read the frontier (8 F_r), write and
     read back each candidate key (16 k F_r), read layers r and r-1 for the set difference
@@ -308,7 +326,9 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": kernel_name,
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(kernel_name) if args.workload == "s11_lrx" else None,
+                     "kernel": kernel_name,
                      "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
                      "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
