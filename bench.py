@@ -143,6 +143,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def combine_ranks(total_ms, units):
+    """Job-wide figures of a multi-rank run: the slowest rank's time (MAX) and all ranks' work
+    (SUM), over the default process group (NCCL on GPUs, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -282,12 +295,10 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    units_all = nb_step * args.steps
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nb_step * args.steps / (total_ms / 1000.0)
+        total_ms, units_all = combine_ranks(total_ms, units_all)
+    value = units_all / (total_ms / 1000.0)
 
     # end to end through the public API: create + run + destroy with host inputs/outputs
     e2e_times = []
@@ -358,7 +369,7 @@ def run_batch(args):
     import paper_2509_19162_gb300 as cg
     cg.build()
     jobs_all = wl.batch_groups()
-    jobs = jobs_all[rank::world]                  # the groups shard across ranks, no exchange
+    jobs = cg.shard(jobs_all, rank, world)        # the groups shard across ranks, no exchange
     spec = [(j.n, j.gens, j.inverse_closed, -1) for j in jobs]
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -396,13 +407,7 @@ def run_batch(args):
     variant = batch.stats()["probe_variant"]
     batch.close()
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        n_all = torch.tensor([nb_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(n_all)
-        nb_all = float(n_all.item())
+        total_ms, nb_all = combine_ranks(total_ms, nb_step)
     else:
         nb_all = nb_step
     value = nb_all * args.steps / (total_ms / 1000.0)

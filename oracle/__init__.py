@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "growth_ref.cpp")
+_SRC_B = os.path.join(_HERE, "growth_bitmap_ref.cpp")
 _LIB = os.path.join(_HERE, "libgrowth_ref.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,9 +30,11 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/libgrowth_ref.so (plain g++, -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_B))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp,
+                               _SRC, _SRC_B])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -52,6 +55,10 @@ def _load():
             lib.oracle_layer_keys.restype = ctypes.c_int
             lib.oracle_distance.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, ctypes.c_int]
             lib.oracle_distance.restype = ctypes.c_int
+            lib.oracle_growth_bitmap.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int,
+                                                 ctypes.c_uint64, ctypes.c_int, u64p, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_growth_bitmap.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -78,6 +85,23 @@ def growth(n: int, gens: Sequence[Sequence[int]], two_layer: bool = False,
                            ctypes.byref(nl))
     if rc < 0:
         raise ValueError(f"oracle_growth failed rc={rc}")
+    return [int(x) for x in out[:nl.value]], rc
+
+
+def growth_bitmap(n: int, gens: Sequence[Sequence[int]], max_radius: int = -1,
+                  stop_above: int = 0, threads: int = 0) -> Tuple[List[int], int]:
+    """Oracle B: the same growth with a visited bitmap over all n! permutations (n <= 14),
+    expanded by `threads` host threads (0: all)."""
+    lib = _load()
+    g = _gens_array(n, gens)
+    cap = 4096
+    out = np.zeros(cap, dtype=np.uint64)
+    nl = ctypes.c_int(0)
+    rc = lib.oracle_growth_bitmap(n, len(gens), _ptr(g, ctypes.c_uint8), int(max_radius),
+                                  int(stop_above), int(threads), _ptr(out, ctypes.c_uint64), cap,
+                                  ctypes.byref(nl))
+    if rc < 0:
+        raise ValueError(f"oracle_growth_bitmap failed rc={rc}")
     return [int(x) for x in out[:nl.value]], rc
 
 

@@ -14,7 +14,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return _build(force=force, verbose=verbose)
 
 
-_API = ("Growth", "GrowthResult", "growth", "Batch", "use_torch_allocator", "STRATEGIES")
+_API = ("Growth", "GrowthResult", "growth", "Batch", "use_torch_allocator", "STRATEGIES", "shard",
+        "unshard")
 
 
 def __getattr__(name):

@@ -231,6 +231,25 @@ class Batch:
             pass
 
 
+def shard(items, rank: int, world: int):
+    """The share of `items` that rank `rank` of `world` runs (round-robin): independent growth
+    jobs shard across GPUs with no exchange step."""
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("need 0 <= rank < world")
+    return items[rank::world]
+
+
+def unshard(parts, total: int):
+    """Inverse of shard: parts[r] is rank r's results in its own order; returns them in the
+    original item order."""
+    world = len(parts)
+    out = [None] * total
+    for r, part in enumerate(parts):
+        for i, x in enumerate(part):
+            out[r + i * world] = x
+    return out
+
+
 _torch_alloc_refs = None
 
 

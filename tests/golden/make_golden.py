@@ -23,20 +23,26 @@ CASES = {
                            "S_14, 13 prefix reversals, layers 0..8 from the identity"),
     "s10_lx_growth": (10, w.lx(10), False, -1,
                                    "S_10, LX generators (directed), full growth"),
+    # oracle B (visited bitmap over all n! ranks): the layers oracle A cannot hold in memory
+    "s14_pancake_layers_b": (14, w.pancake(14), "bitmap", 10,
+                             "S_14, 13 prefix reversals, layers 0..10 from the identity"),
 }
 
 
 def write(name):
     n, gens, two, maxr, desc = CASES[name]
     t0 = time.time()
-    g, rc = oracle.growth(n, gens, two_layer=two, max_radius=maxr)
+    if two == "bitmap":
+        g, rc = oracle.growth_bitmap(n, gens, max_radius=maxr)
+    else:
+        g, rc = oracle.growth(n, gens, two_layer=two, max_radius=maxr)
     dt = time.time() - t0
     path = os.path.join(HERE, name + ".txt")
     with open(path, "w") as f:
         f.write(f"# {desc}\n")
+        mode = "rank-bitmap oracle B" if two == "bitmap" else ("two-layer" if two else "full visited")
         f.write(f"# written by tests/golden/make_golden.py from the CPU oracle "
-                f"({'two-layer' if two else 'full visited'} mode, max_radius={maxr}, "
-                f"{dt:.0f} s)\n")
+                f"({mode} mode, max_radius={maxr}, {dt:.0f} s)\n")
         for r, c in enumerate(g):
             f.write(f"{r} {c}\n")
     print(name, len(g), sum(g), f"{dt:.1f}s")

@@ -257,3 +257,34 @@ def test_limits_and_codes():
     assert oracle.growth(3, [[0, 1, 2]]) == ([1], 0)     # identity generator only
     with pytest.raises(ValueError):
         oracle.growth(3, [[0, 0, 1]])
+
+
+# ---- oracle B (rank-bitmap BFS for large groups) is pinned to oracle A ----------------------
+
+@pytest.mark.parametrize("family", ["coxeter", "lrx", "lx", "pancake", "reversals", "star",
+                                    "three_cycles", "prefix_cycles", "cyclic_coxeter"])
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_oracle_b_equals_oracle_a_on_families(family, n):
+    gens = w.FAMILIES[family](n)
+    if not gens:
+        pytest.skip("empty set")
+    assert oracle.growth_bitmap(n, gens, threads=3) == oracle.growth(n, gens)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_oracle_b_equals_oracle_a_random(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(3, 10))
+    gens = w.random_perms(rng, n, int(rng.integers(1, 4)))
+    if seed % 2:
+        gens = w.inverse_closure(gens)
+    assert oracle.growth_bitmap(n, gens, threads=1 + seed % 4) == oracle.growth(n, gens)
+
+
+def test_oracle_b_limits_and_closed_forms():
+    assert oracle.growth_bitmap(9, w.coxeter(9))[0] == mahonian(9)
+    c = stirling1_unsigned(9)
+    assert oracle.growth_bitmap(9, w.all_transpositions(9))[0] == [c[9 - r] for r in range(9)]
+    assert oracle.growth_bitmap(10, w.lrx(10), max_radius=12) == oracle.growth(10, w.lrx(10), max_radius=12)
+    g, rc = oracle.growth_bitmap(9, w.coxeter(9), stop_above=5000)
+    assert rc == 1 and g == mahonian(9)[:len(g)] and g[-1] > 5000
