@@ -243,3 +243,12 @@ def test_batch_with_hash_visited_sets(cg):
     assert res[0].layers == mahonian(13)[:7] and res[0].status == 1
     assert res[1].layers == oracle.growth(9, w.lrx(9))[0]
     assert res[2].layers == oracle.growth(7, w.lx(7))[0]
+
+
+@pytest.mark.parametrize("strategy", ["bitmap", "hash"])
+def test_config3_s14_pancake_full_size(cg, strategy):
+    # Config 3 at full size: layers 0..10 (2.6e9 states in the last one) against oracle B.
+    job = w.config_s14_pancake()
+    r = cg.growth(job.n, job.gens, True, stop_above=job.stop_above, strategy=strategy)
+    assert r.status == 3                                   # stopped above 2^31
+    assert r.layers == golden("s14_pancake_layers_b")

@@ -288,3 +288,13 @@ def test_oracle_b_limits_and_closed_forms():
     assert oracle.growth_bitmap(10, w.lrx(10), max_radius=12) == oracle.growth(10, w.lrx(10), max_radius=12)
     g, rc = oracle.growth_bitmap(9, w.coxeter(9), stop_above=5000)
     assert rc == 1 and g == mahonian(9)[:len(g)] and g[-1] > 5000
+
+
+def test_stored_values_of_both_oracles_agree():
+    import os
+    d = os.path.join(os.path.dirname(__file__), "golden")
+    read = lambda f: [int(l.split()[1]) for l in open(os.path.join(d, f)) if not l.startswith("#")]
+    a = read("s14_pancake_layers.txt")       # oracle A, layers 0..8
+    b = read("s14_pancake_layers_b.txt")     # oracle B, layers 0..10
+    assert len(a) == 9 and len(b) == 11 and b[:9] == a
+    assert b[10] > 2 ** 31 >= max(b[:10])     # config 3 stops after layer 10
