@@ -6,6 +6,8 @@
 // the visited-state array of a job never needs more than |<S>| entries.
 #include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "group_order.h"
@@ -95,7 +97,36 @@ struct Chain {
 
 }  // namespace
 
+namespace {
+uint64_t group_order_uncached(int n, int k, const uint8_t* gens);
+
+// Orders of recently seen generating sets (the key is n plus the rows as given): serving and
+// batch workloads submit the same named families again and again.
+std::mutex g_cache_mu;
+std::map<std::vector<uint8_t>, uint64_t> g_cache;
+constexpr size_t kCacheMax = 4096;
+}  // namespace
+
 uint64_t group_order(int n, int k, const uint8_t* gens) {
+    std::vector<uint8_t> key;
+    key.reserve(1 + (size_t)n * k);
+    key.push_back((uint8_t)n);
+    key.insert(key.end(), gens, gens + (size_t)n * k);
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) return it->second;
+    }
+    const uint64_t order = group_order_uncached(n, k, gens);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (g_cache.size() >= kCacheMax) g_cache.clear();
+    g_cache.emplace(std::move(key), order);
+    return order;
+}
+
+namespace {
+
+uint64_t group_order_uncached(int n, int k, const uint8_t* gens) {
     Chain C;
     C.n = n;
     std::vector<Perm> S;
@@ -154,5 +185,7 @@ uint64_t group_order(int n, int k, const uint8_t* gens) {
     for (auto& L : C.lv) order *= (uint64_t)L.orbit.size();
     return order;
 }
+
+}  // namespace
 
 }  // namespace cg

@@ -22,7 +22,14 @@ namespace cg {
 namespace {
 
 constexpr int kGrowBlock = 256;
-constexpr uint64_t kMaxProbe = 1ull << 16;   // probe steps (sectors) before giving up
+// Probe steps of one insert before the job is treated as full.  At the table's load limit
+// (0.5) a linear-probing sequence longer than a few dozen slots essentially never occurs; a job
+// whose layer overflows its state array keeps inserting, though, and would otherwise fill the
+// table and scan it.  Hitting the limit marks the job full: the host grows its buffers and
+// redoes the layer, or reports the exact layers so far (CG_TRUNC_MEMCAP).
+constexpr uint64_t kMaxProbe = 64;
+// Bound for re-inserting stored states into a fresh table (load <= 0.5 by construction).
+constexpr uint64_t kMaxProbeRebuild = 1ull << 16;
 
 // Largest j with ubeg[j] <= u (ubeg ascending, ubeg[0] = 0).
 __device__ __forceinline__ int find_job(const unsigned long long* ubeg, int njobs,
@@ -225,7 +232,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                                           overflow_seen, s_cur);
                 // Stop early once any warp found the job's buffers full (the layer will be
                 // redone after the host grows them).
-                if ((++iter & 15u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
+                if ((++iter & 3u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
                     overflow_seen = true;
                 if (overflow_seen) break;
             }
@@ -310,7 +317,7 @@ __global__ void rebuild_table_kernel(const uint64_t* keys, unsigned long long co
                                      uint64_t* table, uint64_t mask, uint64_t key_mask, int* err) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          i < count; i += (unsigned long long)gridDim.x * blockDim.x) {
-        if (table_insert(table, mask, __ldcg(keys + i) & key_mask, kMaxProbe) < 0)
+        if (table_insert(table, mask, __ldcg(keys + i) & key_mask, kMaxProbeRebuild) < 0)
             atomicExch(err, CG_EDEVICE);
     }
 }
