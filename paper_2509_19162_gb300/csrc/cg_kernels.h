@@ -10,7 +10,8 @@ namespace cg {
 
 // hash strategy (hash_path.cu)
 int hash_grow_block();
-int hash_grow_max_grid(int device, int ilp);
+// Co-resident blocks of the persistent kernel variant (multi: launches of several jobs).
+int hash_grow_max_grid(int device, int ilp, bool multi = false);
 // Initialise every job (only_fresh = 0) or only the jobs whose status is kFresh, then lay out
 // the first round's work over all running jobs.
 cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,

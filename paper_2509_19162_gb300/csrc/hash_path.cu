@@ -113,17 +113,91 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
     }
 }
 
+// close_round for a launch with one job, by one thread (no block-wide scan).  Called by every
+// thread of the closing block.
+__device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl) {
+    if (threadIdx.x == 0) {
+        JobDev& J = jobs[0];
+        volatile JobDev& V = jobs[0];
+        unsigned long long units = 0;
+        if (V.status == kRunning) {
+            const unsigned long long tail = ld_relaxed_ull(&J.tail);
+            const unsigned long long hi = V.hi;
+            if (ld_relaxed_int(&J.overflow)) {
+                V.status = kNeedMem;
+            } else {
+                const unsigned long long fresh = tail - hi;
+                if (fresh == 0) {
+                    V.status = kDone;
+                } else {
+                    const int r = V.radius + 1;
+                    J.layer_sizes[r] = fresh;
+                    V.radius = r;
+                    V.lo = hi;
+                    V.hi = tail;
+                    if (J.max_radius >= 0 && r >= J.max_radius) V.status = kTruncRadius;
+                    else if (J.stop_above > 0 && fresh > J.stop_above) V.status = kTruncAbove;
+                    else if (r + 1 >= J.layers_cap) V.status = kTruncRadius;
+                }
+            }
+            if (V.status == kRunning) units = (tail - hi + 31) >> 5;
+        }
+        ubeg[0] = 0;
+        ubeg[1] = units;
+        *(volatile unsigned long long*)&ctl->total_units = units;
+        *(volatile int*)&ctl->rounds += 1;   // one closing thread at a time
+        // After the caller's __syncthreads, this fence makes the block's new states and the
+        // job's new frontier visible device-wide before the next round reads them via L2.
+        __threadfence();
+    }
+    __syncthreads();
+}
+
 // Per-warp staging of newly found states in shared memory: a warp appends its winners to
 // its own buffer and reserves room in the job's key array with one atomic per flush, which
 // turns a per-unit atomic on one global counter into one per ~kStage/32 units and writes the
 // keys out coalesced.
-constexpr int kStage = 256;
+constexpr int kStage = 512;
 
 __device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, int lane) {
     if (cnt == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&J->tail, (unsigned long long)cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
+    uint64_t* keys = J->keys;
+    const unsigned long long cap = J->keys_cap;
+    bool over = false;
+    for (int i = lane; i < cnt; i += 32) {
+        const unsigned long long pos = base + i;
+        if (pos < cap) keys[pos] = buf[i];
+        else over = true;
+    }
+    if (__any_sync(0xffffffffu, over) && lane == 0) atomicExch(&J->overflow, 1);
+    cnt = 0;
+    __syncwarp();
+}
+
+// End-of-round flush of a single job's staged states: one atomicAdd on the job's tail for the
+// whole block (warps take their offsets from a block-level prefix of their counts) instead of
+// one per warp, since same-address atomics serialise at one L2 slice.  Called by every thread
+// of the block.
+__device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDev* J, int lane) {
+    __shared__ unsigned s_cnt[kGrowBlock / 32];
+    __shared__ unsigned long long s_base;
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) s_cnt[w] = (unsigned)cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long total = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            const unsigned c = s_cnt[i];
+            s_cnt[i] = (unsigned)total;
+            total += c;
+        }
+        s_base = total ? atomicAdd(&J->tail, total) : 0;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base + s_cnt[w];
     uint64_t* keys = J->keys;
     const unsigned long long cap = J->keys_cap;
     bool over = false;
@@ -190,58 +264,83 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
     }
 }
 
+// Next work unit of the block for the calling warp (one shared-memory atomic per warp).
+__device__ __forceinline__ unsigned long long draw_unit(unsigned long long& counter, int lane) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(&counter, 1ull);
+    return __shfl_sync(0xffffffffu, u, 0);
+}
+
+// The work phase of a round of a single job, over units [b0, ue) drawn by this block's warps
+// from `s_unit` (set to b0 by the caller, followed by __syncthreads).  Ends with the block's
+// flush of newly found states.  The next unit's frontier key is loaded while the current unit
+// is processed.
+template <int kProbeILP, int kMode>
+__device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsigned long long& s_unit,
+                                             unsigned long long ue, uint64_t* buf, int lane) {
+    const unsigned long long lo = ld_relaxed_ull(&J->lo);
+    const unsigned long long hi = ld_relaxed_ull(&J->hi);
+    int cnt = 0;
+    bool overflow_seen = false;
+    unsigned iter = 0;
+    unsigned long long b = draw_unit(s_unit, lane);
+    uint64_t s_next = (b < ue && lo + (b << 5) + lane < hi) ? __ldcg(J->keys + lo + (b << 5) + lane) : 0;
+    while (b < ue) {
+        const uint64_t s_cur = s_next;
+        const unsigned long long nb = draw_unit(s_unit, lane);
+        s_next = (nb < ue && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
+        do_unit<kProbeILP, kMode>(J, gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen, s_cur);
+        // Stop early once any warp found the job's buffers full (the layer will be redone after
+        // the host grows them).
+        if ((++iter & 3u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
+            overflow_seen = true;
+        if (overflow_seen) break;
+        b = nb;
+    }
+    stage_flush_block(buf, cnt, J, lane);
+}
+
+// Rounds of at most this many units (one per warp of a block) are run by one block alone.
+constexpr unsigned long long kSoloUnits = kGrowBlock / 32;
+
 // Generators of a single job kept in shared memory when there are at most this many.
 constexpr int kSmemGens = 32;
 
-template <int kProbeILP, int kMode>
+// kMulti = false: the launch has exactly one job (the single-job path only is compiled, which
+// keeps registers low); true: any number of jobs.
+template <int kProbeILP, int kMode, bool kMulti>
 __global__ void __launch_bounds__(kGrowBlock, kMode == 2 ? 4 : ((kMode == 1 && kProbeILP >= 3) ? 2 : 3))
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
                  uint64_t timeout_ns) {
     __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
     __shared__ GenSM s_gens[kSmemGens];
+    __shared__ unsigned long long s_unit;
     const GenSM* single_gens = jobs[0].gens;
-    if (njobs == 1 && jobs[0].k <= kSmemGens) {
+    if (!kMulti && jobs[0].k <= kSmemGens) {
         for (int j = threadIdx.x; j < jobs[0].k; j += blockDim.x) s_gens[j] = jobs[0].gens[j];
         __syncthreads();
         single_gens = s_gens;
     }
     const int lane = threadIdx.x & 31;
     uint64_t* buf = s_stage[threadIdx.x >> 5];
-    const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
 
     for (int round = 0; round < max_rounds; ++round) {
         const unsigned long long total = ld_relaxed_ull(&ctl->total_units);
         if (total == 0) break;
+        if (threadIdx.x == 0) s_unit = total * blockIdx.x / gridDim.x;   // this block's first unit
+        __syncthreads();
         int cnt = 0;
         bool overflow_seen = false;
-        if (njobs == 1) {
-            // One job: its frontier is fixed for the round.
-            JobDev* J = jobs;
-            const unsigned long long lo = ld_relaxed_ull(&J->lo);
-            const unsigned long long hi = ld_relaxed_ull(&J->hi);
-            unsigned iter = 0;
-            // The next unit's frontier key is loaded while the current unit is processed.
-            uint64_t s_next = 0;
-            if (warp0 < total && lo + (warp0 << 5) + lane < hi) s_next = __ldcg(J->keys + lo + (warp0 << 5) + lane);
-            for (unsigned long long b = warp0; b < total; b += nwarps) {
-                const uint64_t s_cur = s_next;
-                const unsigned long long nb = b + nwarps;
-                s_next = (nb < total && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
-                do_unit<kProbeILP, kMode>(J, single_gens, lo + (b << 5) + lane, hi, buf, cnt, lane,
-                                          overflow_seen, s_cur);
-                // Stop early once any warp found the job's buffers full (the layer will be
-                // redone after the host grows them).
-                if ((++iter & 3u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
-                    overflow_seen = true;
-                if (overflow_seen) break;
-            }
-            stage_flush(buf, cnt, J, lane);
+        if (!kMulti) {
+            // One job: each block takes a contiguous range of the round's units.
+            phase_single<kProbeILP, kMode>(jobs, single_gens, s_unit, total * (blockIdx.x + 1) / gridDim.x,
+                                           buf, lane);
         } else {
             int cur = -1;
             JobDev* J = nullptr;
             unsigned long long lo = 0, hi = 0, u0 = 0;
-            for (unsigned long long u = warp0; u < total; u += nwarps) {
+            const unsigned long long ue = total * (blockIdx.x + 1) / gridDim.x;
+            for (unsigned long long u = draw_unit(s_unit, lane); u < ue; u = draw_unit(s_unit, lane)) {
                 const int j = find_job(ubeg, njobs, u);
                 if (j != cur) {
                     if (J) stage_flush(buf, cnt, J, lane);
@@ -267,7 +366,23 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         const int arrive = grid_arrive(ctl, timeout_ns);
         if (arrive < 0) return;
         if (arrive == 1) {
-            close_round(jobs, njobs, ubeg, ctl);
+            if (!kMulti) {
+                close_round_single(jobs, ubeg, ctl);
+                // While the frontier stays small this block runs the next rounds alone, with
+                // __syncthreads for a barrier; the other blocks wait until it releases them.
+                for (;;) {
+                    const unsigned long long t = *(volatile unsigned long long*)&ctl->total_units;
+                    if (t == 0 || t > kSoloUnits || round + 1 >= max_rounds) break;
+                    ++round;
+                    if (threadIdx.x == 0) s_unit = 0;
+                    __syncthreads();
+                    phase_single<kProbeILP, kMode>(jobs, single_gens, s_unit, t, buf, lane);
+                    __syncthreads();
+                    close_round_single(jobs, ubeg, ctl);
+                }
+            } else {
+                close_round(jobs, njobs, ubeg, ctl);
+            }
             grid_release(ctl);
         }
     }
@@ -381,29 +496,32 @@ int hash_grow_block() { return kGrowBlock; }
 namespace {
 using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t);
 // Kernel variants: `ilp` generators per thread (1..4); +8 selects whole-sector table probing,
-// +16 the rank bitmap.
-GrowFn grow_fn(int variant) {
+// +16 the rank bitmap; multi = launches of several jobs.
+template <bool M>
+GrowFn grow_fn_t(int variant) {
     switch (variant) {
-        case 1: return hash_grow_kernel<1, 0>;
-        case 2: return hash_grow_kernel<2, 0>;
-        case 3: return hash_grow_kernel<3, 0>;
-        case 4: return hash_grow_kernel<4, 0>;
-        case 9: return hash_grow_kernel<1, 1>;
-        case 10: return hash_grow_kernel<2, 1>;
-        case 11: return hash_grow_kernel<3, 1>;
-        case 12: return hash_grow_kernel<4, 1>;
-        case 17: return hash_grow_kernel<1, 2>;
-        case 18: return hash_grow_kernel<2, 2>;
-        case 19: return hash_grow_kernel<3, 2>;
-        default: return hash_grow_kernel<4, 2>;
+        case 1: return hash_grow_kernel<1, 0, M>;
+        case 2: return hash_grow_kernel<2, 0, M>;
+        case 3: return hash_grow_kernel<3, 0, M>;
+        case 4: return hash_grow_kernel<4, 0, M>;
+        case 9: return hash_grow_kernel<1, 1, M>;
+        case 10: return hash_grow_kernel<2, 1, M>;
+        case 11: return hash_grow_kernel<3, 1, M>;
+        case 12: return hash_grow_kernel<4, 1, M>;
+        case 17: return hash_grow_kernel<1, 2, M>;
+        case 18: return hash_grow_kernel<2, 2, M>;
+        case 19: return hash_grow_kernel<3, 2, M>;
+        default: return hash_grow_kernel<4, 2, M>;
     }
 }
+
+GrowFn grow_fn(int variant, bool multi) { return multi ? grow_fn_t<true>(variant) : grow_fn_t<false>(variant); }
 }  // namespace
 
-int hash_grow_max_grid(int device, int ilp) {
+int hash_grow_max_grid(int device, int ilp, bool multi) {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grow_fn(ilp), kGrowBlock, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grow_fn(ilp, multi), kGrowBlock, 0) !=
         cudaSuccess)
         return 0;
     return sms * per_sm;
@@ -434,7 +552,7 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, grow_fn(ilp), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
+    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, njobs > 1), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
                               timeout_ns);
 }
 

@@ -222,14 +222,15 @@ int status_to_rc(int status) {
     }
 }
 
-int device_grid_cache[64][32] = {};
+int device_grid_cache[64][32][2] = {};
 
 // Blocks of the persistent kernel that fit co-resident on device `dev` (variant: ILP 1..4, +8
-// for whole-sector table probing, +16 for the rank bitmap).
-int grow_grid(int dev, int ilp) {
+// for whole-sector table probing, +16 for the rank bitmap; multi: several jobs per launch).
+int grow_grid(int dev, int ilp, bool multi = false) {
     if (dev < 0 || dev >= 64 || ilp < 1 || ilp > 20) return 0;
-    if (!device_grid_cache[dev][ilp]) device_grid_cache[dev][ilp] = cg::hash_grow_max_grid(dev, ilp);
-    return device_grid_cache[dev][ilp];
+    int& c = device_grid_cache[dev][ilp][multi ? 1 : 0];
+    if (!c) c = cg::hash_grow_max_grid(dev, ilp, multi);
+    return c;
 }
 
 // Generators probed together per thread.  Hash tables (random DRAM probes): all of them when
@@ -1028,7 +1029,7 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     const int ilp = default_ilp(maxk, any_bitmap) + (any_bitmap ? 16 : 0);
     b->stats.strategy_used = any_bitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
     b->stats.probe_variant = ilp;
-    const int grid = grow_grid(dev, ilp);
+    const int grid = grow_grid(dev, ilp, true);
     if (grid <= 0) return CG_ECUDA;
     const uint64_t budget = b->mem_cap;
     const uint64_t per_job_max = max_cap_for_mem(budget / 2);
@@ -1300,7 +1301,7 @@ int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finis
                 any_bitmap |= sl.job.mode == cg::kVisitBitmap;
             }
         const int variant = default_ilp(maxk, any_bitmap) + (any_bitmap ? 16 : 0);
-        const int grid = grow_grid(s->device, variant);
+        const int grid = grow_grid(s->device, variant, true);
         if (grid <= 0) return CG_ECUDA;
         cudaError_t e;
         if ((e = cudaMemsetAsync(s->d_ctl, 0, sizeof(Ctl), st))) return cuda_rc(e);

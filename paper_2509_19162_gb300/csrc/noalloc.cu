@@ -60,7 +60,7 @@ int setup_device(int dev) {
         cudaGetLastError();
         return CG_ECUDA;
     }
-    const int grid = cg::hash_grow_max_grid(dev, 1);
+    const int grid = cg::hash_grow_max_grid(dev, 1, false);
     if (grid <= 0) return CG_ECUDA;
     g_scratch_addr[dev] = static_cast<unsigned char*>(p);
     g_grid[dev] = grid;
