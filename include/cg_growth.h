@@ -101,6 +101,16 @@ typedef struct cg_growth* cg_growth_t;
 int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
                      uint64_t mem_cap, cg_growth_t* out);
 
+/*
+ * Grow from a central state instead of the identity (Section 3.1.2: a Schreier coset graph is
+ * given by a vector whose stabiliser is the subgroup; its growth is that of the vector's orbit,
+ * Section 5.2).  start: host pointer, n values in 0..15, repeats allowed; copied.  NULL restores
+ * the identity.  A start with repeated values needs the HASH or SORT strategy (AUTO picks HASH;
+ * BITMAP then fails at run with CG_EINVAL).  Releases buffers sized for an earlier start.
+ * Errors: CG_EINVAL.
+ */
+int cg_growth_set_start(cg_growth_t h, const uint8_t* start);
+
 /* Set an option (CG_OPT_*) before cg_growth_run.  Errors: CG_EINVAL. */
 int cg_growth_set_option(cg_growth_t h, int option, int64_t value);
 

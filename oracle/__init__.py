@@ -50,6 +50,10 @@ def _load():
                                           ctypes.c_int, ctypes.c_uint64, u64p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]
             lib.oracle_growth.restype = ctypes.c_int
+            lib.oracle_growth_from.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_uint64, u64p, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_growth_from.restype = ctypes.c_int
             lib.oracle_layer_keys.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int,
                                               u64p, ctypes.c_uint64, u64p]
             lib.oracle_layer_keys.restype = ctypes.c_int
@@ -73,16 +77,21 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def growth(n: int, gens: Sequence[Sequence[int]], two_layer: bool = False,
-           max_radius: int = -1, stop_above: int = 0) -> Tuple[List[int], int]:
-    """Growth vector gamma(0..R) and the return code (0 ended, 1 stopped by a limit)."""
+           max_radius: int = -1, stop_above: int = 0, start=None) -> Tuple[List[int], int]:
+    """Growth vector gamma(0..R) and the return code (0 ended, 1 stopped by a limit), from the
+    identity or from the vector `start` (n values in 0..15, repeats allowed)."""
     lib = _load()
     g = _gens_array(n, gens)
     cap = 4096
     out = np.zeros(cap, dtype=np.uint64)
     nl = ctypes.c_int(0)
-    rc = lib.oracle_growth(n, len(gens), _ptr(g, ctypes.c_uint8), int(two_layer),
-                           int(max_radius), int(stop_above), _ptr(out, ctypes.c_uint64), cap,
-                           ctypes.byref(nl))
+    st = None
+    if start is not None:
+        st = np.ascontiguousarray(np.asarray(start, dtype=np.uint8))
+    rc = lib.oracle_growth_from(n, len(gens), _ptr(g, ctypes.c_uint8),
+                                _ptr(st, ctypes.c_uint8) if st is not None else None,
+                                int(two_layer), int(max_radius), int(stop_above),
+                                _ptr(out, ctypes.c_uint64), cap, ctypes.byref(nl))
     if rc < 0:
         raise ValueError(f"oracle_growth failed rc={rc}")
     return [int(x) for x in out[:nl.value]], rc

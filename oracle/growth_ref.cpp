@@ -21,7 +21,10 @@
  * the group order (sympy's Schreier-Sims and brute-force closure), palindromic Coxeter
  * growth, published diameters (Section 3.3 table, Section 3.4 maximal-diameter tables,
  * Section 4 LX conjecture, Section 5.2 reversal sphere |S_2|), and all-pairs shortest paths
- * of the explicit graph for n <= 5.
+ * of the explicit graph for n <= 5.  The coset mode (growth from a vector with repeated
+ * entries) is pinned in tests/test_oracle_coset_pins.py: all-pairs shortest paths of the
+ * explicit coset graph, orbit sizes, and the God's numbers the paper prints for the binary
+ * coset (Section 3.2 and the Schreier-graph table).
  */
 #include <cstdint>
 #include <cstring>
@@ -66,10 +69,12 @@ struct Bfs {
     uint64_t frontier_count = 0;
     int radius = 0;
 
-    Bfs(int n_, int k_, const uint8_t* g_, bool two)
+    // Breadth-first search from `start` (n values, repeats allowed: the orbit of a vector under
+    // the group, i.e. a Schreier coset graph, Sections 3.1.2 and 5.2), or from the identity.
+    Bfs(int n_, int k_, const uint8_t* g_, bool two, const uint8_t* start = nullptr)
         : n(n_), k(k_), gens(g_), two_layer(two) {
         frontier.resize(n);
-        for (int i = 0; i < n; ++i) frontier[i] = (uint8_t)i;
+        for (int i = 0; i < n; ++i) frontier[i] = start ? start[i] : (uint8_t)i;
         frontier_count = 1;
         uint64_t id = key_of(frontier.data(), n);
         if (two_layer) cur.insert(id); else seen.insert(id);
@@ -113,7 +118,8 @@ struct Bfs {
 extern "C" {
 
 /*
- * Growth vector of <gens> from the identity.
+ * Growth vector of <gens> from the identity (oracle_growth) or from the vector `start`
+ * (oracle_growth_from; n values in 0..15, repeats allowed).
  *   two_layer   0: full visited set (any generating set); 1: keep only layers r-1 and r
  *               (correct only for inverse-closed sets; the tests check it against mode 0).
  *   max_radius  < 0: unlimited; else stop after layer max_radius.
@@ -122,10 +128,13 @@ extern "C" {
  * Returns 0 when the growth ended (empty next layer), 1 when stopped by max_radius or
  * stop_above, -1 on invalid input, -2 when cap was too small (*num_layers still exact).
  */
-int oracle_growth(int n, int k, const uint8_t* gens, int two_layer, int max_radius,
-                  uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
+int oracle_growth_from(int n, int k, const uint8_t* gens, const uint8_t* start, int two_layer,
+                       int max_radius, uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
     if (!valid_gens(n, k, gens) || num_layers == nullptr) return -1;
-    Bfs bfs(n, k, gens, two_layer != 0);
+    if (start)
+        for (int i = 0; i < n; ++i)
+            if (start[i] > 15) return -1;
+    Bfs bfs(n, k, gens, two_layer != 0, start);
     std::vector<uint64_t> layers{1};
     int rc = 0;
     while (true) {
@@ -139,6 +148,12 @@ int oracle_growth(int n, int k, const uint8_t* gens, int two_layer, int max_radi
     for (int r = 0; r < (int)layers.size() && r < cap; ++r) out[r] = layers[r];
     if ((int)layers.size() > cap) return -2;
     return rc;
+}
+
+int oracle_growth(int n, int k, const uint8_t* gens, int two_layer, int max_radius,
+                  uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
+    return oracle_growth_from(n, k, gens, nullptr, two_layer, max_radius, stop_above, out, cap,
+                              num_layers);
 }
 
 /*

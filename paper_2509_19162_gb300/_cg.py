@@ -55,6 +55,7 @@ SIGNATURES = {
     "cg_growth_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_uint64, ctypes.POINTER(_vp)]),
     "cg_growth_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
+    "cg_growth_set_start": (ctypes.c_int, [_vp, _u8p]),
     "cg_growth_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip]),
     "cg_growth_last_layer": (ctypes.c_int, [_vp, _u64p, ctypes.c_uint64, _u64p]),
     "cg_growth_group_order": (ctypes.c_uint64, [_vp]),
@@ -126,6 +127,7 @@ def _export(name):
 cg_set_allocator = _export("cg_set_allocator")
 cg_growth_create = _export("cg_growth_create")
 cg_growth_set_option = _export("cg_growth_set_option")
+cg_growth_set_start = _export("cg_growth_set_start")
 cg_growth_run = _export("cg_growth_run")
 cg_growth_last_layer = _export("cg_growth_last_layer")
 cg_growth_group_order = _export("cg_growth_group_order")

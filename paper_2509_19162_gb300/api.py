@@ -41,6 +41,26 @@ class GrowthResult:
     def total(self) -> int:
         return int(sum(self.layers))
 
+    def statistics(self) -> dict:
+        """Moments of the distance distribution P(d = r) = |S_r| / sum |S_r| (the growth
+        columns of the paper's Section 3.3 table): mean, mode, variance, skewness and excess
+        kurtosis.  Computed on the host from the exact layer sizes, with exact integer sums."""
+        from fractions import Fraction
+        N = sum(self.layers)
+        if N == 0:
+            return {}
+        m1 = Fraction(sum(r * c for r, c in enumerate(self.layers)), N)
+        var = Fraction(sum((r - m1) ** 2 * c for r, c in enumerate(self.layers)), N)
+        m3 = Fraction(sum((r - m1) ** 3 * c for r, c in enumerate(self.layers)), N)
+        m4 = Fraction(sum((r - m1) ** 4 * c for r, c in enumerate(self.layers)), N)
+        mode = max(range(len(self.layers)), key=lambda r: (self.layers[r], -r))
+        out = {"mean": float(m1), "mode": mode, "variance": float(var),
+               "skewness": 0.0, "kurtosis": 0.0, "diameter": self.diameter}
+        if var > 0:
+            out["skewness"] = float(m3) / float(var) ** 1.5
+            out["kurtosis"] = float(m4 / (var * var)) - 3.0
+        return out
+
 
 def _stream_handle(stream) -> Optional[int]:
     if stream is None:
@@ -78,7 +98,9 @@ class Growth:
 
     def __init__(self, n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool] = None,
                  max_radius: int = -1, mem_cap: int = 0, strategy: str = "auto",
-                 stop_above: int = 0, keep_last: bool = False):
+                 stop_above: int = 0, keep_last: bool = False, start: Optional[Sequence[int]] = None):
+        """start: a central state (n values in 0..15, repeats allowed) to grow the orbit of,
+        i.e. a Schreier coset graph; None grows the Cayley graph from the identity."""
         g = _gens_bytes(n, gens)
         if inverse_closed is None:
             inverse_closed = _is_inverse_closed(gens)
@@ -101,6 +123,8 @@ class Growth:
         if keep_last:
             _cg.check(_cg.cg_growth_set_option(h, _cg.CG_OPT_KEEP_LAST, 1),
                       "cg_growth_set_option(keep_last)")
+        if start is not None:
+            self.set_start(start)
         self._cap = 1024
         self._out = np.zeros(self._cap, dtype=np.uint64)
 
@@ -121,6 +145,19 @@ class Growth:
             break
         _cg.check(rc, "cg_growth_run")
         return GrowthResult([int(x) for x in self._out[:nl.value]], rc)
+
+    def set_start(self, start: Optional[Sequence[int]]) -> None:
+        """Grow from the central state `start` (n values in 0..15, repeats allowed: a Schreier
+        coset graph), or from the identity when None."""
+        if start is None:
+            _cg.check(_cg.cg_growth_set_start(self._h, None), "cg_growth_set_start")
+            return
+        st = np.ascontiguousarray(np.asarray(start, dtype=np.int64))
+        if st.shape != (self.n,) or st.min(initial=0) < 0 or st.max(initial=0) > 15:
+            raise ValueError("start must hold n values in 0..15")
+        st8 = st.astype(np.uint8)
+        _cg.check(_cg.cg_growth_set_start(self._h, st8.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+                  "cg_growth_set_start")
 
     def set_grid(self, blocks: int) -> None:
         """Blocks of the persistent launch (0 = library default)."""
@@ -163,9 +200,10 @@ class Growth:
 
 def growth(n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool] = None,
            max_radius: int = -1, mem_cap: int = 0, strategy: str = "auto", stop_above: int = 0,
-           stream=None) -> GrowthResult:
-    """Growth vector |S_0|, |S_1|, ... of the Cayley graph of <gens> from the identity."""
-    with Growth(n, gens, inverse_closed, max_radius, mem_cap, strategy, stop_above) as g:
+           stream=None, start: Optional[Sequence[int]] = None) -> GrowthResult:
+    """Growth vector |S_0|, |S_1|, ... of the Cayley graph of <gens> from the identity, or of
+    the Schreier coset graph of the orbit of `start`."""
+    with Growth(n, gens, inverse_closed, max_radius, mem_cap, strategy, stop_above, start=start) as g:
         return g.run(stream)
 
 

@@ -57,8 +57,9 @@ struct alignas(128) JobDev {
     int layers_cap;
     int max_radius;            // < 0: unlimited
     int mode;                  // visited set: 0 hash table, 2 rank bitmap (kVisitBitmap)
-    int pad0;
+    int use_start;             // 1: grow from start_key (a central state), 0: from the identity
     uint64_t bitmap_words;     // bitmap mode: 32-bit words in `table` (ceil(n!/32))
+    uint64_t start_key;        // packed start vector when use_start
     // dynamic, updated between rounds by block 0
     alignas(128) unsigned long long lo;     // frontier = keys[lo, hi)
     unsigned long long hi;

@@ -396,9 +396,14 @@ __global__ void init_jobs_kernel(JobDev* jobs, int njobs, int only_fresh) {
     if (only_fresh && J.status != kFresh) return;
     uint64_t id = 0;
     for (int i = 0; i < J.n; ++i) id |= (uint64_t)i << (4 * i);
+    if (J.use_start) id = J.start_key;      // a central state: the growth of its orbit
     J.keys[0] = id;
-    if (J.mode == kVisitBitmap) atomicOr(reinterpret_cast<unsigned*>(J.table), 1u);  // rank(e) = 0
-    else table_insert(J.table, J.table_mask, id, kMaxProbe);
+    if (J.mode == kVisitBitmap) {
+        const uint64_t r = perm_rank(id, J.n);
+        atomicOr(reinterpret_cast<unsigned*>(J.table) + (r >> 5), 1u << (unsigned)(r & 31u));
+    } else {
+        table_insert(J.table, J.table_mask, id, kMaxProbe);
+    }
     J.layer_sizes[0] = 1;
     J.lo = 0;
     J.hi = 1;

@@ -254,6 +254,10 @@ struct cg_growth {
     int grid_override = 0;
     int ilp_override = 0;
     int mode = -1;                               // visited set chosen at the first run
+    bool use_start = false;                      // grow from a central state instead of e
+    uint64_t start_key = 0;
+    bool start_is_perm = true;                   // the start vector has distinct entries
+    uint64_t states_bound = 1;                   // states the growth can reach (orbit bound)
     uint64_t order = 1;
     int device = -1;
     cudaStream_t alloc_stream = nullptr;
@@ -296,6 +300,9 @@ struct cg_growth {
         d_layers = nullptr; d_keys = nullptr; d_table = nullptr;
         keys_cap = table_slots = 0;
         release_sort(st);
+        have_last = false;                 // the last layer lived in the freed buffers
+        last_layer_ptr = nullptr;
+        last_layer_n = 0;
     }
 
     void release_sort(cudaStream_t st) {
@@ -375,6 +382,8 @@ void fill_static(cg_growth* h, JobDev& J) {
     J.max_radius = h->max_radius;
     J.mode = h->mode;
     J.bitmap_words = h->mode == cg::kVisitBitmap ? bitmap_words(h->n) : 0;
+    J.use_start = h->use_start ? 1 : 0;
+    J.start_key = h->start_key;
 }
 
 int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
@@ -384,19 +393,23 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     if (fresh_alloc) h->stats.h2d_bytes += sizeof(GenSM) * h->k;
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
     if (h->mode < 0) {
-        if (h->strategy == CG_STRATEGY_BITMAP && !bitmap_fits(h->n, mem)) return CG_EINVAL;
+        // the rank bitmap indexes permutations: a start vector with repeated entries needs the
+        // hash table
+        if (h->strategy == CG_STRATEGY_BITMAP && (!bitmap_fits(h->n, mem) || !h->start_is_perm))
+            return CG_EINVAL;
         h->mode = (h->strategy == CG_STRATEGY_BITMAP ||
-                   (h->strategy == CG_STRATEGY_AUTO && bitmap_eligible(h->n, h->order, mem)))
+                   (h->strategy == CG_STRATEGY_AUTO && h->start_is_perm &&
+                    bitmap_eligible(h->n, h->order, mem)))
                       ? cg::kVisitBitmap : cg::kVisitHash;
     }
     const bool bitmap = h->mode == cg::kVisitBitmap;
     const uint64_t avail = mem > (1 << 20) ? mem - (1 << 20) : mem;
     const uint64_t bm_bytes = bitmap ? bitmap_words(h->n) * 4 : 0;
     const uint64_t max_cap = std::min<uint64_t>(
-        h->order, bitmap ? (avail > bm_bytes ? (avail - bm_bytes) / 8 : 0) : max_cap_for_mem(avail));
+        h->states_bound, bitmap ? (avail > bm_bytes ? (avail - bm_bytes) / 8 : 0) : max_cap_for_mem(avail));
     if (max_cap < 1) return CG_ENOMEM;
     if (!h->d_keys) {
-        uint64_t start = h->order;
+        uint64_t start = h->states_bound;
         const uint64_t need = bitmap ? start * 8 + bm_bytes : bytes_for(start);
         if (need > std::min<uint64_t>(mem, kExactAllocLimit))
             start = std::min<uint64_t>(max_cap, 1ull << 24);
@@ -408,7 +421,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     const int grid_max = grow_grid(h->device, ilp);
     if (grid_max <= 0) return CG_ECUDA;
     // Small groups finish faster with fewer blocks at each barrier.
-    const uint64_t want = h->order / (32 * 8 * 2) + 1;
+    const uint64_t want = h->states_bound / (32 * 8 * 2) + 1;
     int grid = (int)std::min<uint64_t>((uint64_t)grid_max, std::max<uint64_t>(want, 1));
     if (h->grid_override > 0) grid = std::min(grid_max, h->grid_override);
 
@@ -507,7 +520,7 @@ int ensure_sort_buffers(cg_growth* h, uint64_t need_layer, uint64_t need_cand, u
         if (!h->d_cand || !h->d_sort_scratch) return CG_ENOMEM;
     }
     if (need_layer > h->L_cap) {
-        uint64_t cap = std::max<uint64_t>(need_layer, std::min<uint64_t>(need_layer * 2, h->order));
+        uint64_t cap = std::max<uint64_t>(need_layer, std::min<uint64_t>(need_layer * 2, h->states_bound));
         if (3 * cap * 8 + h->cand_cap * 8 + cg::sort_scratch_bytes(h->cand_cap) > mem) cap = need_layer;
         if (3 * cap * 8 + h->cand_cap * 8 + cg::sort_scratch_bytes(h->cand_cap) > mem) return CG_TRUNC_MEMCAP;
         for (int i = 0; i < 3; ++i) {
@@ -542,6 +555,7 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
     if (rc) return rc < 0 ? rc : CG_ENOMEM;
     uint64_t id = 0;
     for (int i = 0; i < h->n; ++i) id |= (uint64_t)i << (4 * i);
+    if (h->use_start) id = h->start_key;
     cudaError_t e = cudaMemcpyAsync(h->d_L[cur], &id, 8, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_rc(e);
     h->stats.h2d_bytes += 8;
@@ -644,7 +658,45 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
     std::vector<uint8_t> flat;
     for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
     h->order = rows.empty() ? 1 : cg::group_order(n, (int)rows.size(), flat.data());
+    h->states_bound = h->order;
     *out = h;
+    return CG_OK;
+}
+
+int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
+    if (!h) return CG_EINVAL;
+    int count[16] = {0};
+    uint64_t key = 0;
+    if (start)
+        for (int i = 0; i < h->n; ++i) {
+            if (start[i] > 15) return CG_EINVAL;
+            count[start[i]]++;
+            key |= (uint64_t)start[i] << (4 * i);
+        }
+    if (h->device >= 0) {                 // buffers were sized for the previous start
+        h->release(nullptr);
+        cudaStreamSynchronize(nullptr);
+    }
+    h->mode = -1;
+    if (!start) {
+        h->use_start = false;
+        h->start_key = 0;
+        h->start_is_perm = true;
+        h->states_bound = h->order;
+        return CG_OK;
+    }
+    // The orbit of the start vector has at most as many states as the group, and at most as
+    // many as the distinct rearrangements of the vector (a multinomial coefficient).
+    uint64_t rearr = factorial(h->n);
+    bool perm = true;
+    for (int v = 0; v < 16; ++v) {
+        rearr /= factorial(count[v]);
+        perm &= count[v] <= 1;
+    }
+    h->use_start = true;
+    h->start_key = key;
+    h->start_is_perm = perm;
+    h->states_bound = std::min(h->order, rearr);
     return CG_OK;
 }
 

@@ -75,6 +75,18 @@ def test_create_validation(lib):
     lib.cg_growth_destroy(h)
 
 
+def test_set_start_validation(lib):
+    rc, h = _create(lib, 5, w.lrx(5), inv=1)
+    u8 = ctypes.POINTER(ctypes.c_uint8)
+    bad = np.array([0, 1, 2, 3, 16], dtype=np.uint8)
+    ok = np.array([0, 0, 1, 1, 1], dtype=np.uint8)
+    assert lib.cg_growth_set_start(None, ok.ctypes.data_as(u8)) == lib.CG_EINVAL
+    assert lib.cg_growth_set_start(h, bad.ctypes.data_as(u8)) == lib.CG_EINVAL
+    assert lib.cg_growth_set_start(h, ok.ctypes.data_as(u8)) == 0
+    assert lib.cg_growth_set_start(h, None) == 0
+    lib.cg_growth_destroy(h)
+
+
 def test_group_order_closed_forms(lib):
     from paper_2509_19162_gb300 import Growth
     for n in range(2, 17):

@@ -1,0 +1,92 @@
+"""GPU parity of Schreier coset growth (growth of the orbit of a central state, Section 3.1.2
+and Section 3.2) through the C ABI, against the oracle and against closed forms at sizes the
+oracle does not reach in seconds."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from test_oracle_coset_pins import q_multinomial
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2509_19162_gb300 as p
+    p.build()
+    return p
+
+
+@pytest.mark.parametrize("strategy", ["hash", "auto", "sort"])
+@pytest.mark.parametrize("seed", range(16))
+def test_random_cosets_vs_oracle(cg, seed, strategy):
+    rng = np.random.default_rng(4000 + seed)
+    n = int(rng.integers(2, 13))
+    gens = w.random_perms(rng, n, int(rng.integers(1, 4)))
+    if strategy == "sort" or seed % 2 == 0:
+        gens = w.inverse_closure(gens)
+    start = [int(x) for x in rng.integers(0, int(rng.integers(1, n + 1)), size=n)]
+    want, _ = oracle.growth(n, gens, start=start)
+    got = cg.growth(n, gens, strategy=strategy, start=start)
+    assert got.status == 0
+    assert got.layers == want
+
+
+@pytest.mark.parametrize("family", ["lrx", "pancake", "transposons", "reversals", "coxeter",
+                                    "consecutive_4cycles", "star", "lx"])
+@pytest.mark.parametrize("n", [5, 12, 16])
+def test_binary_cosets_vs_oracle(cg, family, n):
+    gens = w.FAMILIES[family](n)
+    start = w.binary_start(n)
+    want, _ = oracle.growth(n, gens, start=start)
+    for strategy in ("hash", "auto"):
+        assert cg.growth(n, gens, strategy=strategy, start=start).layers == want
+
+
+@pytest.mark.parametrize("strategy", ["hash", "bitmap", "sort"])
+def test_permutation_start_is_a_copy_of_the_group(cg, strategy):
+    # distinct entries: the orbit is the regular action, growth equal to that from e
+    rng = np.random.default_rng(7)
+    for n, gens in [(9, w.lrx(9)), (8, w.pancake(8)), (10, w.coxeter(10))]:
+        perm = [int(x) for x in rng.permutation(n)]
+        assert cg.growth(n, gens, strategy=strategy, start=perm).layers == oracle.growth(n, gens)[0]
+
+
+def test_bitmap_rejects_repeated_entries_and_start_resets(cg):
+    g = cg.Growth(8, w.coxeter(8), strategy="bitmap", start=w.binary_start(8))
+    with pytest.raises(RuntimeError):
+        g.run()
+    g.close()
+    g = cg.Growth(8, w.coxeter(8), start=w.binary_start(8), keep_last=True)
+    r = g.run()
+    assert r.layers == q_multinomial((4, 4))
+    assert list(np.sort(g.last_layer())) == [sum(v << (4 * i) for i, v in enumerate([1] * 4 + [0] * 4))]
+    g.set_start(None)
+    assert g.run().layers == oracle.growth(8, w.coxeter(8))[0]
+    g.set_start([3, 3, 2, 2, 1, 1, 0, 0])
+    assert g.run().layers == q_multinomial((2, 2, 2, 2))
+    g.close()
+
+
+@pytest.mark.parametrize("strategy", ["hash", "sort"])
+def test_full_size_multiset_orbit_is_q_multinomial(cg, strategy):
+    # 16 entries, four values four times each: 16! / (4!)^4 = 63,063,000 states, growth the
+    # Gaussian multinomial [16; 4,4,4,4]_q (adjacent transpositions count inversions).
+    counts = (4, 4, 4, 4)
+    start = [v for v, c in enumerate(counts) for _ in range(c)]
+    r = cg.growth(16, w.coxeter(16), strategy=strategy, start=start)
+    assert r.status == 0
+    assert r.total == math.factorial(16) // math.factorial(4) ** 4
+    assert r.layers == q_multinomial(counts)
+
+
+def test_binary_coset_n16_lrx_closed_form(cg):
+    g = cg.growth(16, w.lrx(16), start=w.binary_start(16))
+    assert len(g.layers) - 1 == (16 * 44 + 32) // 16
+    assert g.total == math.comb(16, 8)

@@ -9,7 +9,9 @@ its output as plain lists of integers.
 from .families import (  # noqa: F401
     FAMILIES,
     all_transpositions,
+    binary_start,
     consecutive_3cycles_inv,
+    consecutive_4cycles,
     coxeter,
     cycle,
     cycles_01i_inv,

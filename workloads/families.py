@@ -188,6 +188,19 @@ def prefix_cycles(n: int) -> List[Perm]:
     return [cycle(n, list(range(i + 1))) for i in range(1, n)]
 
 
+def consecutive_4cycles(n: int) -> List[Perm]:
+    """Consecutive 4-cycles (i, i+1, i+2, i+3), i = 0..n-4 (directed; Section 3.2, acting on
+    binary vectors)."""
+    return [cycle(n, [i, i + 1, i + 2, i + 3]) for i in range(n - 3)]
+
+
+def binary_start(n: int) -> List[int]:
+    """Central state of the "Bin" coset S_n / (S_m x S_{n-m}), m = floor(n/2): m zeros, then
+    ones (Section 3.2 and the Schreier-graph table)."""
+    m = n // 2
+    return [0] * m + [1] * (n - m)
+
+
 def koltsov3(n: int, type_: int, k: int, d: int = 1) -> List[Perm]:
     """Koltsov3involutions (Section 3.7): I = prod_{i even}(i,i+1), K = prod_{i odd}(i,i+1),
     and S = (k, k+d) for type 1 or S = (k, k+3)(k+1, k+2) for type 2."""
@@ -232,4 +245,5 @@ FAMILIES: Dict[str, Callable[[int], List[Perm]]] = {
     "cycles_01i_inv": cycles_01i_inv,
     "consecutive_3cycles_inv": consecutive_3cycles_inv,
     "prefix_cycles": prefix_cycles,
+    "consecutive_4cycles": consecutive_4cycles,
 }
