@@ -47,20 +47,21 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def measured_traffic(kernel_name):
-    """DRAM bytes per launch of `kernel_name` from the committed ncu record (profiles/traffic.json),
-    or None when there is none or the kernel's sources changed since it was taken."""
+def measured_traffic(kernel_name, workload):
+    """DRAM bytes per launch of `kernel_name` on `workload` from the committed ncu record
+    (profiles/traffic.json), or None when there is none or the kernel's sources changed since it
+    was taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel_name)
-        if not rec:
+        if not rec or rec.get("workload") != workload:
             return None
         h = hashlib.sha256()
         for src in rec["kernel_sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
-        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["kernel_sources_sha256"] else None
+        return rec["dram_bytes"] if h.hexdigest() == rec["kernel_sources_sha256"] else None
     except Exception:
         return None
 
@@ -249,7 +250,7 @@ def run_ours(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
 
     handle = cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
-                       stop_above=job.stop_above, keep_last=False)
+                       stop_above=job.stop_above, keep_last=False, strategy=args.strategy)
     # warm-up (also allocates the job's buffers: inputs resident before the timed region)
     res = None
     for _ in range(args.warmup):
@@ -277,7 +278,7 @@ def run_ours(args):
     st0 = handle.stats()
     strat_name = {1: "hash", 2: "sort", 3: "bitmap"}.get(st0["strategy_used"], "?")
     variant = st0["probe_variant"]
-    kernel_name = (f"hash_grow_kernel<{variant & 7}, {variant >> 3}>" if strat_name != "sort"
+    kernel_name = (f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 0>" if strat_name != "sort"
                    else "radix sort / merge-path kernels")
     for i in range(args.steps):
         flush.zero_()                               # evict L2 between timed steps
@@ -308,7 +309,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
-                       stop_above=job.stop_above) as g:
+                       stop_above=job.stop_above, strategy=args.strategy) as g:
             r = g.run(stream)
             st = g.stats()
         e2e_times.append(time.perf_counter() - t0)
@@ -333,12 +334,14 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": job.name, "n": job.n, "k": job.k, "states": sum(layers),
                    "layers": len(layers), "neighbours_per_step": nb_step,
-                   "strategy": strat_name + " (visited set; one persistent cooperative launch)",
+                   "strategy": strat_name + (" (visited set; one persistent cooperative launch)"
+                                             if strat_name != "sort" else
+                                             " (sorted layers: expand, radix sort, merge-path difference)"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": measured_traffic(kernel_name) if args.workload == "s11_lrx" else None,
+                     "traffic": measured_traffic(kernel_name, job.name),
                      "kernel": kernel_name,
                      "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
                      "peak_source": peak_kind},
@@ -443,8 +446,11 @@ def run_batch(args):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "groups sharded over ranks" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}> (multi-job)",
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1>",
+                                                 f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}"),
+                     "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1> (multi-job, "
+                               f"{launches // (3 * args.steps)} launches per batch run)",
                      "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind},
         "e2e": {"value": nb_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": est["h2d_bytes"],
                 "d2h_bytes_per_step": est["d2h_bytes"], "api": "paper_2509_19162_gb300.Batch(...).run()"},
@@ -519,6 +525,8 @@ def main():
     ap.add_argument("--workload", default="s11_lrx",
                     choices=["s11_lrx", "s8_coxeter", "s14_pancake", "batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--strategy", default="auto", choices=["auto", "hash", "bitmap", "sort"],
+                    help="visited-set strategy of the single-job workloads")
     ap.add_argument("--serve-jobs", type=int, default=20000)
     ap.add_argument("--serve-job-mem", type=int, default=64, help="per-job device memory cap, MiB")
     ap.add_argument("--serve-slots", type=int, default=512)

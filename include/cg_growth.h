@@ -189,6 +189,17 @@ int cg_batch_create(int njobs, const int* n, const int* k, const uint8_t* gens,
 int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int cap,
                  int* num_layers_out, int* status_out);
 
+/*
+ * Cap on the summed visited-set bytes (rank bitmaps and hash tables) of the jobs that one launch
+ * of cg_batch_run grows together.  Every candidate state costs one random access to its job's
+ * visited set; while the sets of the running jobs fit in L2 those accesses stay on chip, so the
+ * batch is split into launches ("waves") whose sets fit.  A job whose set alone exceeds the cap
+ * does not count against it.  bytes = 0: half of the device's L2 (the default);
+ * UINT64_MAX: no cap (waves bounded by the memory budget only).  No paper counterpart: the
+ * paper grows one graph at a time.  Errors: CG_EINVAL.
+ */
+int cg_batch_set_wave_l2(cg_batch_t b, uint64_t bytes);
+
 /* Measurements of the last cg_batch_run (as cg_growth_get_stats).  Errors: CG_EINVAL. */
 int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "cg_batch_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip, _ip]),
     "cg_batch_destroy": (ctypes.c_int, [_vp]),
     "cg_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(cg_growth_stats)]),
+    "cg_batch_set_wave_l2": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "cg_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.POINTER(_vp)]),
     "cg_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int, _u64p]),
@@ -138,6 +139,7 @@ cg_batch_create = _export("cg_batch_create")
 cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")
 cg_batch_get_stats = _export("cg_batch_get_stats")
+cg_batch_set_wave_l2 = _export("cg_batch_set_wave_l2")
 cg_server_create = _export("cg_server_create")
 cg_server_submit = _export("cg_server_submit")
 cg_server_step = _export("cg_server_step")

@@ -210,8 +210,9 @@ def growth(n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool]
 class Batch:
     """Many independent growth jobs run together (cg_batch_create ... cg_batch_destroy)."""
 
-    def __init__(self, jobs, mem_cap: int = 0):
-        """jobs: sequence of (n, gens, inverse_closed, max_radius)."""
+    def __init__(self, jobs, mem_cap: int = 0, wave_l2: Optional[int] = None):
+        """jobs: sequence of (n, gens, inverse_closed, max_radius).  wave_l2: cap on the summed
+        visited-set bytes grown in one launch (None: half of L2; -1: no cap)."""
         self.njobs = len(jobs)
         ns = np.array([j[0] for j in jobs], dtype=np.int32)
         ks = np.array([len(j[1]) for j in jobs], dtype=np.int32)
@@ -231,6 +232,14 @@ class Batch:
                                       inv.ctypes.data_as(ip), rad.ctypes.data_as(ip), int(mem_cap),
                                       ctypes.byref(h)), "cg_batch_create")
         self._h = h
+        if wave_l2 is not None:
+            self.set_wave_l2(wave_l2)
+
+    def set_wave_l2(self, nbytes: int) -> None:
+        """Cap on the summed visited-set bytes of the jobs grown in one launch (0: half of L2,
+        -1: no cap)."""
+        v = (1 << 64) - 1 if nbytes < 0 else int(nbytes)
+        _cg.check(_cg.cg_batch_set_wave_l2(self._h, v), "cg_batch_set_wave_l2")
 
     def stats(self) -> dict:
         st = _cg.cg_growth_stats()

@@ -911,6 +911,7 @@ struct cg_batch {
     };
     std::vector<Job> jobs;
     uint64_t mem_cap = kDefaultMemCap;
+    uint64_t wave_l2 = 0;          // cap on summed visited-set bytes per launch; 0: L2 / 2
     cg_growth_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -1085,15 +1086,27 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     if (grid <= 0) return CG_ECUDA;
     const uint64_t budget = b->mem_cap;
     const uint64_t per_job_max = max_cap_for_mem(budget / 2);
-    // Greedy waves in job order, each within the memory budget.
+    uint64_t l2_cap = b->wave_l2;
+    if (l2_cap == 0) {
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) {
+            cudaGetLastError();
+            l2 = 64 << 20;
+        }
+        l2_cap = (uint64_t)l2 / 2;
+    }
+    // Greedy waves in job order, each within the memory budget and with visited sets that
+    // together fit the L2 cap (a set larger than the cap misses L2 wherever it runs and does not
+    // count).
     std::vector<int> wave;
-    uint64_t wave_bytes = 0;
+    uint64_t wave_bytes = 0, wave_vis = 0;
     int rc = CG_OK;
     auto flush = [&]() {
         int r = run_wave(b, wave, st, layer_sizes_out, cap, num_layers_out, status_out, grid, ilp);
         if (r != CG_OK && rc == CG_OK) rc = r;
         wave.clear();
         wave_bytes = 0;
+        wave_vis = 0;
     };
     for (int j = 0; j < (int)b->jobs.size(); ++j) {
         auto& J = b->jobs[j];
@@ -1104,15 +1117,24 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
             continue;
         }
         J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
-        const uint64_t vis = J.mode == cg::kVisitBitmap ? J.cap * 8 + bitmap_words(J.n) * 4 : bytes_for(J.cap);
-        const uint64_t need = vis + sizeof(GenSM) * J.gsm.size() + sizeof(JobDev) +
-                              (uint64_t)(cap + 1) * 8 + 1024;
-        if (!wave.empty() && wave_bytes + need > budget) flush();
+        const uint64_t set_bytes = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) * 4
+                                                               : table_slots_for(J.cap) * 8;
+        const uint64_t need = J.cap * 8 + set_bytes + sizeof(GenSM) * J.gsm.size() +
+                              sizeof(JobDev) + (uint64_t)(cap + 1) * 8 + 1024;
+        const uint64_t vis = set_bytes <= l2_cap ? set_bytes : 0;
+        if (!wave.empty() && (wave_bytes + need > budget || wave_vis + vis > l2_cap)) flush();
         wave.push_back(j);
         wave_bytes += need;
+        wave_vis += vis;
     }
     if (!wave.empty()) flush();
     return rc;
+}
+
+int cg_batch_set_wave_l2(cg_batch_t b, uint64_t bytes) {
+    if (!b) return CG_EINVAL;
+    b->wave_l2 = bytes;
+    return CG_OK;
 }
 
 int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out) {

@@ -190,7 +190,25 @@ def test_batch_radius_caps_and_waves(cg):
             assert r.layers == oracle.growth(7, w.lx(7))[0]
 
 
-def test_step_expand_matches_gather(cg):
+@pytest.mark.parametrize("wave_l2", [1 << 10, 256 << 10, 0, -1])
+def test_batch_l2_waves_give_the_same_results(cg, wave_l2):
+    # the L2 cap only changes how jobs are grouped into launches, never a result
+    jobs = w.batch_groups(count=64)
+    spec = [(j.n, j.gens, j.inverse_closed, -1) for j in jobs]
+    with cg.Batch(spec, wave_l2=wave_l2) as b:
+        res = b.run()
+        launches = b.stats()["launches"]
+    with cg.Batch(spec, wave_l2=-1) as b:
+        ref = b.run()
+    assert [r.layers for r in res] == [r.layers for r in ref]
+    for j, r in list(zip(jobs, res))[:24:3]:
+        assert r.layers == oracle.growth(j.n, j.gens)[0]
+    if wave_l2 == -1:
+        assert launches == 3                # one launch (plus its two setup kernels)
+    if wave_l2 == 256 << 10:
+        assert launches > 3                 # the n <= 9 bitmaps (<= 45 KB) fill several waves
+
+
     import torch
     from paper_2509_19162_gb300 import _cg
     rng = np.random.default_rng(5)
