@@ -171,6 +171,13 @@ def get_workload(name):
         return wl.config_s8_coxeter()
     if name == "s14_pancake":
         return wl.config_s14_pancake()
+    if ":" in name:
+        # any named family, full growth: e.g. "pancake:14" (the whole of S_14), "coxeter:13"
+        fam, n = name.split(":")
+        n = int(n)
+        gens = wl.FAMILIES[fam](n)
+        return wl.GrowthJob(n, gens, wl.is_inverse_closed(gens), name=f"S{n}-{fam}-k{len(gens)}-full",
+                            family=fam)
     raise ValueError(name)
 
 
@@ -192,8 +199,23 @@ def oracle_sample(job, radius):
     return neighbours(layers, job.k, complete), dt, layers, complete
 
 
+def sample_radius(job, budget_s):
+    """Largest radius whose oracle growth ends within about budget_s (for workloads without a
+    fixed sample): radii are tried in order until one takes more than a quarter of the budget."""
+    import oracle
+    R = 1
+    while True:
+        t0 = time.perf_counter()
+        _, rc = oracle.growth(job.n, job.gens, max_radius=R)
+        if rc == 0:
+            return -1
+        if time.perf_counter() - t0 > budget_s / 4:
+            return R
+        R += 1
+
+
 def cpu_baseline(wname, job):
-    R = ORACLE_SAMPLE_RADIUS.get(wname, -1)
+    R = ORACLE_SAMPLE_RADIUS[wname] if wname in ORACLE_SAMPLE_RADIUS else sample_radius(job, 20.0)
     nb, dt, layers, complete = oracle_sample(job, R)
     return {"value": nb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{job.name}: growth to radius {len(layers) - 1} "
@@ -207,7 +229,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     job = get_workload(args.workload)
-    R = REFERENCE_STEP_RADIUS.get(args.workload, -1)
+    R = (REFERENCE_STEP_RADIUS[args.workload] if args.workload in REFERENCE_STEP_RADIUS
+         else sample_radius(job, 10.0))
     for _ in range(args.warmup):
         oracle_sample(job, R)
     total_nb, total_t = 0, 0.0
@@ -276,10 +299,11 @@ def run_ours(args):
     kernel_ms = 0.0
     launches = 0
     st0 = handle.stats()
-    strat_name = {1: "hash", 2: "sort", 3: "bitmap"}.get(st0["strategy_used"], "?")
+    strat_name = {1: "hash", 2: "sort", 3: "bitmap", 4: "sweep"}.get(st0["strategy_used"], "?")
     variant = st0["probe_variant"]
-    kernel_name = (f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 0>" if strat_name != "sort"
-                   else "radix sort / merge-path kernels")
+    kernel_name = {"sort": "radix sort / merge-path kernels",
+                   "sweep": f"sweep_grow_kernel<{variant}>"}.get(
+        strat_name, f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 0>")
     for i in range(args.steps):
         flush.zero_()                               # evict L2 between timed steps
         torch.cuda.synchronize()
@@ -334,9 +358,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": job.name, "n": job.n, "k": job.k, "states": sum(layers),
                    "layers": len(layers), "neighbours_per_step": nb_step,
-                   "strategy": strat_name + (" (visited set; one persistent cooperative launch)"
-                                             if strat_name != "sort" else
-                                             " (sorted layers: expand, radix sort, merge-path difference)"),
+                   "strategy": strat_name + {
+                       "sort": " (sorted layers: expand, radix sort, merge-path difference)",
+                       "sweep": " (bitmaps over S_n for the visited set and layers; one persistent "
+                                "cooperative launch)"}.get(
+                       strat_name, " (visited set; one persistent cooperative launch)"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -523,9 +549,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="s11_lrx",
-                    choices=["s11_lrx", "s8_coxeter", "s14_pancake", "batch", "serve"])
+                    help="s11_lrx | s8_coxeter | s14_pancake | batch | serve | <family>:<n> "
+                         "(full growth of a named family, e.g. pancake:14)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--strategy", default="auto", choices=["auto", "hash", "bitmap", "sort"],
+    ap.add_argument("--strategy", default="auto", choices=["auto", "hash", "bitmap", "sort", "sweep"],
                     help="visited-set strategy of the single-job workloads")
     ap.add_argument("--serve-jobs", type=int, default=20000)
     ap.add_argument("--serve-job-mem", type=int, default=64, help="per-job device memory cap, MiB")

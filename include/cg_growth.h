@@ -47,7 +47,8 @@ extern "C" {
                                   cg_growth_run_noalloc (CG_NOALLOC_MAX_*)                    */
 
 /* ---- strategies (cg_growth_set_option(h, CG_OPT_STRATEGY, ...)) --------------------- */
-#define CG_STRATEGY_AUTO    0  /* library chooses: BITMAP when eligible, else HASH            */
+#define CG_STRATEGY_AUTO    0  /* library chooses: BITMAP when eligible, SWEEP when the states
+                                  of BITMAP do not fit but the sweep's bitmaps do, else HASH  */
 #define CG_STRATEGY_HASH    1  /* visited open-addressing hash set; any generating set        */
 #define CG_STRATEGY_SORT    2  /* sorted layers, radix sort + unique + merge-path difference
                                   against layers r and r-1; inverse-closed sets only          */
@@ -56,6 +57,12 @@ extern "C" {
                                   most half of mem_cap and 16 GiB (else CG_EINVAL at run).
                                   AUTO picks it when it fits and the group fills at least 1/512
                                   of S_n, else HASH                                           */
+#define CG_STRATEGY_SWEEP   4  /* bitmask BFS (Section 3.1.3): the visited set and the last
+                                  three layers are bitmaps over the n! Lehmer ranks (4 bits per
+                                  element of S_n, nothing per state), so the whole of S_14 fits
+                                  in 44 GB; any generating set; start with distinct values;
+                                  needs n <= 14 and the bitmaps within mem_cap (else CG_EINVAL
+                                  at run)                                                      */
 
 /* ---- options ------------------------------------------------------------------------ */
 #define CG_OPT_STRATEGY     1  /* one of CG_STRATEGY_*                                        */
@@ -321,6 +328,21 @@ int cg_set_difference(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_
                       const uint64_t* c, uint64_t nc, uint64_t* out, uint64_t* d_count,
                       void* scratch, size_t scratch_bytes, void* cuda_stream);
 int cg_hash_clear(uint64_t* table, uint64_t slots, void* cuda_stream);
+
+/*
+ * Index of a permutation in the sweep strategy's bitmaps (the bitmask BFS of Section 3.1.3):
+ * the position-major Lehmer rank  rank(s) = sum_{i=1}^{n-1} d_i * i!,  d_i = #{j < i : s_j < s_i},
+ * a bijection from S_n onto 0..n!-1 (identity -> n!-1, full reversal -> 0).
+ * cg_perm_rank: keys (device, count packed permutations of 0..n-1, element i in bits 4i..4i+3)
+ *   -> ranks (device, count).  A key that is not a permutation of 0..n-1 gives an unspecified
+ *   value.
+ * cg_perm_unrank: ranks (device, count values < n!) -> keys (device).  A rank >= n! gives an
+ *   unspecified key.
+ * 1 <= n <= 16.  Asynchronous on the stream.  Errors: CG_EINVAL (n out of range, null pointer
+ * with count > 0), CG_ECUDA.
+ */
+int cg_perm_rank(int n, const uint64_t* keys, uint64_t count, uint64_t* ranks, void* cuda_stream);
+int cg_perm_unrank(int n, const uint64_t* ranks, uint64_t count, uint64_t* keys, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ CG_STRATEGY_AUTO = 0
 CG_STRATEGY_HASH = 1
 CG_STRATEGY_SORT = 2
 CG_STRATEGY_BITMAP = 3
+CG_STRATEGY_SWEEP = 4
 
 CG_OPT_STRATEGY = 1
 CG_OPT_STOP_ABOVE = 2
@@ -81,6 +82,8 @@ SIGNATURES = {
     "cg_expand": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_hash_insert": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
     "cg_hash_clear": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp]),
+    "cg_perm_rank": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_uint64, _vp, _vp]),
+    "cg_perm_unrank": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_sort_unique_scratch_bytes": (ctypes.c_size_t, [ctypes.c_uint64]),
     "cg_sort_unique": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "cg_set_difference": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, ctypes.c_uint64,
@@ -140,6 +143,8 @@ cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")
 cg_batch_get_stats = _export("cg_batch_get_stats")
 cg_batch_set_wave_l2 = _export("cg_batch_set_wave_l2")
+cg_perm_rank = _export("cg_perm_rank")
+cg_perm_unrank = _export("cg_perm_unrank")
 cg_server_create = _export("cg_server_create")
 cg_server_submit = _export("cg_server_submit")
 cg_server_step = _export("cg_server_step")

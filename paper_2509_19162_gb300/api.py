@@ -21,7 +21,7 @@ import numpy as np
 from . import _cg
 
 STRATEGIES = {"auto": _cg.CG_STRATEGY_AUTO, "hash": _cg.CG_STRATEGY_HASH, "sort": _cg.CG_STRATEGY_SORT,
-              "bitmap": _cg.CG_STRATEGY_BITMAP}
+              "bitmap": _cg.CG_STRATEGY_BITMAP, "sweep": _cg.CG_STRATEGY_SWEEP}
 
 
 @dataclass

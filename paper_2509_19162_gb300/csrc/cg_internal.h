@@ -70,6 +70,34 @@ struct alignas(128) JobDev {
     int pad;
 };
 
+// One growth of the sweep strategy: the visited set and the last three layers are bitmaps over
+// the position-major Lehmer ranks 0..n!-1 (one bit per element of S_n).  Layer r lives in
+// F[r % 3]; its nonempty 1024-rank blocks (32 words of F) are listed, once each, in
+// L[r % 3][0, lcount[r % 3]); S[r % 3] has one bit per block and is what makes a block's entry
+// in the list unique.
+struct alignas(128) SweepDev {
+    // static, written by the host
+    unsigned* V;               // visited
+    unsigned* F[3];            // layers r-1, r, r+1 in rotation
+    unsigned* S[3];            // per-block bits of F (one bit per 32 words)
+    unsigned* L[3];            // nonempty blocks of F (block index = rank >> 10)
+    const GenSM* gens;         // k entries
+    uint64_t* layer_sizes;     // layers_cap entries; [0] = 1
+    uint64_t nblocks;          // 1024-rank blocks: every F has 32 * nblocks words
+    uint64_t stop_above;       // 0: none
+    uint64_t start_rank;       // rank of the start state
+    int k;
+    int n;
+    int layers_cap;
+    int max_radius;            // < 0: unlimited
+    // dynamic, updated during a run
+    alignas(128) unsigned long long grab;   // next work item of the round
+    unsigned long long fresh;               // states found in the round
+    unsigned long long lcount[3];           // entries of L[i]
+    int radius;                // radius of the frontier layer
+    int status;                // JobStatus
+};
+
 // Control block of the persistent kernel (device memory, zero-initialised by the host).
 // Blocks arrive at the grid barrier on kBarGroups group counters, the last of each group on
 // the top counter; every counter and the generation word that waiting blocks poll sit in

@@ -32,4 +32,20 @@ cudaError_t launch_hash_insert(uint64_t* table, uint64_t mask, const uint64_t* k
                                unsigned long long N, uint64_t* out, unsigned long long* count,
                                int* fail, int grid, cudaStream_t st);
 
+// sweep strategy (sweep_path.cu)
+int sweep_max_grid(int device, int ilp);
+cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st);
+cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
+                              int ilp, cudaStream_t st);
+// Unrank the states of one layer (bitmap F, block list L[0, nlist)) into out[0, cap); *count
+// (zeroed by the caller) receives the number of states.
+cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,
+                                uint64_t* out, unsigned long long cap, unsigned long long* count,
+                                int grid, cudaStream_t st);
+// Position-major Lehmer rank of packed permutations, and its inverse.
+cudaError_t launch_pos_rank(const uint64_t* keys, unsigned long long count, int n, uint64_t* out,
+                            int grid, cudaStream_t st);
+cudaError_t launch_pos_unrank(const uint64_t* ranks, unsigned long long count, int n, uint64_t* out,
+                              int grid, cudaStream_t st);
+
 }  // namespace cg

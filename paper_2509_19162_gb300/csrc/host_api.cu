@@ -23,11 +23,14 @@
 using cg::Ctl;
 using cg::GenSM;
 using cg::JobDev;
+using cg::SweepDev;
 
 namespace {
 
 constexpr uint64_t kDefaultMemCap = 160ull << 30;
 constexpr uint64_t kTimeoutNs = 30ull * 1000 * 1000 * 1000;  // per barrier wait
+// A sweep round of all of S_14 can take seconds; a block with no work waits that long.
+constexpr uint64_t kSweepTimeoutNs = 120ull * 1000 * 1000 * 1000;
 constexpr double kMaxLoad = 0.5;                                // visited-table load limit
 constexpr uint64_t kExactAllocLimit = 24ull << 30;  // allocate |<S>| states up front below this
 
@@ -176,6 +179,15 @@ uint64_t factorial(int n) {
     return f;
 }
 
+// Sweep strategy layout over S_n: 1024-rank blocks, and the bytes of V, three layer bitmaps,
+// their block bits and block lists.
+uint64_t sweep_blocks(int n) { return (factorial(n) + 1023) / 1024; }
+uint64_t sweep_bytes(int n) {
+    const uint64_t nb = sweep_blocks(n);
+    const uint64_t words = nb * 32, sum = (nb + 31) / 32;
+    return 4 * (4 * words + 3 * sum + 3 * nb) + 4096;
+}
+
 // 32-bit words of a rank bitmap over S_n, rounded up to whole 8-byte slots.
 uint64_t bitmap_words(int n) { return ((factorial(n) + 63) / 64) * 2; }
 
@@ -283,6 +295,13 @@ struct cg_growth {
     uint64_t last_layer_n = 0;
     std::vector<uint64_t> sort_layers;
 
+    // sweep strategy: visited bitmap, three layer bitmaps with block bits and block lists
+    SweepDev* d_sweep = nullptr;
+    unsigned* d_sw = nullptr;                    // one allocation holding all of the below
+    uint64_t sw_bytes = 0;
+    SweepDev host_sweep{};
+    bool last_is_sweep = false;
+
     JobDev host_job{};
     bool have_last = false;
     cg_growth_stats stats{};
@@ -299,6 +318,11 @@ struct cg_growth {
         d_gens = nullptr; d_job = nullptr; d_ctl = nullptr; d_ubeg = nullptr;
         d_layers = nullptr; d_keys = nullptr; d_table = nullptr;
         keys_cap = table_slots = 0;
+        dev_free(d_sweep, st);
+        dev_free(d_sw, st);
+        d_sweep = nullptr;
+        d_sw = nullptr;
+        sw_bytes = 0;
         release_sort(st);
         have_last = false;                 // the last layer lived in the freed buffers
         last_layer_ptr = nullptr;
@@ -492,6 +516,116 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     *final_status = J.status;
     h->last_layer_ptr = h->d_keys + J.lo;
     h->last_layer_n = J.hi - J.lo;
+    return CG_OK;
+}
+
+// ---- sweep strategy driver -----------------------------------------------------------------
+// Bitmaps over S_n for the visited set and the last three layers (sweep_path.cu); one
+// persistent launch runs every layer step.  Needs a start with distinct values and n <= 14.
+
+// AUTO takes the sweep for the whole growth (no radius or layer-size limit) of a dense subgroup
+// of S_n whose states, stored as keys beside a rank bitmap, would not fit the memory cap while
+// the sweep's bitmaps do.  With a limit the key-list path runs first: it is faster while the
+// states it stores fit, and grows its buffers as the layers come.
+bool sweep_preferred(const cg_growth* h) {
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    if (!h->start_is_perm || h->n > 14 || h->n < 2) return false;
+    if (h->max_radius >= 0 || h->stop_above > 0) return false;
+    if (h->order * 512 < factorial(h->n)) return false;
+    if (sweep_bytes(h->n) > mem) return false;
+    return h->states_bound * 8 + bitmap_words(h->n) * 4 > mem;
+}
+
+int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    if (!h->start_is_perm || h->n > 14 || h->n < 1) return CG_EINVAL;
+    const uint64_t bytes = sweep_bytes(h->n);
+    if (bytes > mem) return CG_EINVAL;
+    int rc = ensure_small_buffers(h, st);
+    if (rc) return rc;
+    const uint64_t nb = sweep_blocks(h->n);
+    const uint64_t words = nb * 32, nsum = (nb + 31) / 32;
+    if (!h->d_sw) {
+        h->d_sw = (unsigned*)dev_alloc(bytes, st);
+        h->d_sweep = (SweepDev*)dev_alloc(sizeof(SweepDev), st);
+        if (!h->d_sw || !h->d_sweep) return CG_ENOMEM;
+        h->sw_bytes = bytes;
+    }
+    // layout: V | F0 F1 F2 | S0 S1 S2 | L0 L1 L2   (32-bit words)
+    SweepDev D;
+    std::memset(&D, 0, sizeof(D));
+    unsigned* p = h->d_sw;
+    D.V = p; p += words;
+    for (int i = 0; i < 3; ++i) { D.F[i] = p; p += words; }
+    for (int i = 0; i < 3; ++i) { D.S[i] = p; p += nsum; }
+    for (int i = 0; i < 3; ++i) { D.L[i] = p; p += nb; }
+    D.gens = h->d_gens;
+    D.layer_sizes = h->d_layers;
+    D.nblocks = nb;
+    D.stop_above = h->stop_above;
+    D.k = h->k;
+    D.n = h->n;
+    D.layers_cap = cg::kMaxLayers;
+    D.max_radius = h->max_radius < 0 ? -1 : h->max_radius;
+    // rank of the start (identity: 0), position-major Lehmer digits taken from the top down
+    {
+        uint8_t v[16];
+        for (int i = 0; i < h->n; ++i)
+            v[i] = h->use_start ? (uint8_t)((h->start_key >> (4 * i)) & 15u) : (uint8_t)i;
+        uint64_t r = 0;
+        unsigned right = 0;
+        for (int i = h->n - 1; i >= 1; --i) {
+            unsigned d = v[i];
+            for (unsigned u = 0; u < v[i]; ++u) d -= (right >> u) & 1u;
+            right |= 1u << v[i];
+            r = r * (uint64_t)(i + 1) + d;
+        }
+        D.start_rank = r;
+    }
+    // V, F and S start empty (the lists need no clearing: lcount bounds them)
+    cudaError_t e = cudaMemsetAsync(D.V, 0, (4 * words + 3 * nsum) * 4, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(h->d_sweep, &D, sizeof(D), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cg::launch_sweep_init(h->d_sweep, st)) != cudaSuccess) return cuda_rc(e);
+    h->stats.launches += 1;
+    h->stats.h2d_bytes += sizeof(D);
+    // two generators in flight per thread measured best (S_12 Coxeter, S_13 pancake)
+    const int ilp = h->ilp_override > 0 ? h->ilp_override : std::min(h->k, 2);
+    int grid = cg::sweep_max_grid(h->device, ilp);
+    if (grid <= 0) return CG_ECUDA;
+    if (h->grid_override > 0) grid = std::min(grid, h->grid_override);
+    if (!h->ev0) {
+        if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
+    }
+    if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cg::launch_sweep_grow(h->d_sweep, h->d_ctl, grid, cg::kMaxLayers + 1, kSweepTimeoutNs, ilp,
+                                   st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
+    h->stats.launches += 1;
+    Ctl ctl;
+    if ((e = cudaMemcpyAsync(&D, h->d_sweep, sizeof(D), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaMemcpyAsync(&ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_rc(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+    h->stats.d2h_bytes += sizeof(D) + sizeof(ctl);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->stats.kernel_ms += ms;
+    h->stats.rounds += ctl.rounds;
+    if (ctl.err) return ctl.err;
+    h->stats.state_capacity = factorial(h->n);
+    h->stats.table_slots = words / 2;
+    h->stats.strategy_used = CG_STRATEGY_SWEEP;
+    h->stats.probe_variant = ilp;
+    h->host_sweep = D;
+    std::memset(&h->host_job, 0, sizeof(h->host_job));
+    h->host_job.radius = D.radius;
+    h->host_job.status = D.status;
+    *final_status = D.status;
     return CG_OK;
 }
 
@@ -704,7 +838,7 @@ int cg_growth_set_option(cg_growth_t h, int option, int64_t value) {
     if (!h) return CG_EINVAL;
     switch (option) {
         case CG_OPT_STRATEGY:
-            if (value < CG_STRATEGY_AUTO || value > CG_STRATEGY_BITMAP) return CG_EINVAL;
+            if (value < CG_STRATEGY_AUTO || value > CG_STRATEGY_SWEEP) return CG_EINVAL;
             if (value == CG_STRATEGY_SORT && !h->inverse_closed) return CG_EINVAL;
             if (value != h->strategy && h->device >= 0) {   // buffers are laid out per strategy
                 h->release(nullptr);
@@ -752,8 +886,12 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
     h->device = dev;
     int status = 0;
     const bool use_sort = h->strategy == CG_STRATEGY_SORT;
-    int rc = use_sort ? run_sort(h, st, &status) : run_hash(h, st, &status);
+    const bool use_sweep = h->strategy == CG_STRATEGY_SWEEP ||
+                           (h->strategy == CG_STRATEGY_AUTO && sweep_preferred(h));
+    int rc = use_sort ? run_sort(h, st, &status)
+                      : use_sweep ? run_sweep(h, st, &status) : run_hash(h, st, &status);
     if (rc) return rc;
+    h->last_is_sweep = use_sweep;
     const int layers = h->host_job.radius + 1;
     *num_layers_out = layers;
     if (cap < layers) return CG_EINVAL;
@@ -772,6 +910,33 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
 
 int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64_t* count_out) {
     if (!h || !count_out || !h->have_last) return CG_EINVAL;
+    if (h->last_is_sweep) {
+        // unrank the last layer's bitmap (layer R lives in F[R % 3], its blocks in L[R % 3])
+        const SweepDev& D = h->host_sweep;
+        uint64_t cnt = 0;
+        cudaError_t e = cudaMemcpy(&cnt, h->d_layers + D.radius, 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_rc(e);
+        *count_out = cnt;
+        if (cap < cnt || (!keys_out && cnt > 0)) return CG_EINVAL;
+        if (cnt == 0) return CG_OK;
+        uint64_t* d_out = (uint64_t*)dev_alloc(cnt * 8 + 64, nullptr);
+        if (!d_out) return CG_ENOMEM;
+        unsigned long long* d_count = (unsigned long long*)(d_out + cnt);
+        const int w = D.radius % 3;
+        int grid = 0;
+        cudaDeviceGetAttribute(&grid, cudaDevAttrMultiProcessorCount, h->device);
+        e = cudaMemsetAsync(d_count, 0, 8, nullptr);
+        if (e == cudaSuccess)
+            e = cg::launch_sweep_export(D.F[w], D.L[w], D.lcount[w], h->n, d_out, cnt, d_count,
+                                        std::max(grid, 1) * 8, nullptr);
+        unsigned long long got = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&got, d_count, 8, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(keys_out, d_out, cnt * 8, cudaMemcpyDeviceToHost);
+        dev_free(d_out, nullptr);
+        cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) return cuda_rc(e);
+        return got == cnt ? CG_OK : CG_EDEVICE;
+    }
     const uint64_t cnt = h->last_layer_n;
     *count_out = cnt;
     if (cap < cnt || (!keys_out && cnt > 0)) return CG_EINVAL;
@@ -875,6 +1040,24 @@ int cg_set_difference(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_
     if (e == cudaSuccess)
         e = cg::launch_unique_difference(a, na, bs, ns, 2, out, (unsigned long long*)d_count, sc, st);
     return cuda_rc(e);
+}
+
+int cg_perm_rank(int n, const uint64_t* keys, uint64_t count, uint64_t* ranks, void* cuda_stream) {
+    if (n < 1 || n > 16 || (count > 0 && (!keys || !ranks))) return CG_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CG_ECUDA;
+    return cuda_rc(cg::launch_pos_rank(keys, count, n, ranks, sms * 8, (cudaStream_t)cuda_stream));
+}
+
+int cg_perm_unrank(int n, const uint64_t* ranks, uint64_t count, uint64_t* keys, void* cuda_stream) {
+    if (n < 1 || n > 16 || (count > 0 && (!keys || !ranks))) return CG_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CG_ECUDA;
+    return cuda_rc(cg::launch_pos_unrank(ranks, count, n, keys, sms * 8, (cudaStream_t)cuda_stream));
 }
 
 int cg_hash_clear(uint64_t* table, uint64_t slots, void* cuda_stream) {

@@ -1,0 +1,462 @@
+// Sweep strategy of the growth library: breadth-first growth with the visited set and the
+// layers held as bitmaps over S_n, the paper's bitmask BFS (Section 3.1.3: a few bits per
+// element of the group instead of a list of states).  Nothing per state is stored but bits, so a
+// growth needs 4 n!/8 bytes whatever its layers hold: 43.6 GB for all of S_14.
+//
+// Index of a permutation: the position-major Lehmer rank
+//     rank(s) = sum_{i=1}^{n-1} d_i * i!,   d_i = #{ j < i : s_j < s_i },
+// a bijection S_n -> [0, n!).  A generator that moves only positions below j changes only the
+// digits below j, so its image lies within j! ranks of the state: prefix reversals, adjacent
+// transpositions and other short-support generators keep their visited-set accesses close to
+// the block being expanded, which the L2 serves.
+//
+// One round (layer step) of the persistent cooperative kernel:
+//   work units 0 .. 32|L_r|-1: a word (32 ranks) of a nonempty 1024-rank block of layer r.  Its
+//       states are unranked, every generator applied, the images ranked and test-and-set in V
+//       (one atomicOr each); a new state sets its bit in F_{r+1}, the first bit of a block
+//       enters the block in L_{r+1} (per-warp staging, one atomic per 32 entries);
+//   work units 32|L_r| .. 32|L_r|+|L_{r-1}|-1: a block of layer r-1, cleared (F and S), so that
+//       its buffers are empty when they receive layer r+2;
+//   grid barrier; the last block to arrive records |L_{r+1}| and the stop tests.
+// Units are drawn by warps from one counter in decreasing chunks (guided scheduling).
+#include <cstdio>
+
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+namespace cg {
+
+namespace {
+
+constexpr int kSweepBlock = 256;
+constexpr int kSweepWarps = kSweepBlock / 32;
+constexpr int kSweepSmemGens = 32;
+constexpr int kListStage = 64;   // staged block-list entries per warp
+
+__host__ __device__ constexpr uint64_t fact(int i) { return i <= 1 ? 1ull : (uint64_t)i * fact(i - 1); }
+
+// rank(s) for a packed permutation of 0..n-1 (element i in bits 4i..4i+3), n <= 16.  Digits are
+// taken from the top position down: d_i = s_i - #{j > i : s_j < s_i}.  The digits of positions
+// 12.. and 1..11 are combined in two 32-bit Horner sums (both fit), then joined.
+__device__ __forceinline__ uint64_t pos_rank(uint64_t key, int n) {
+    unsigned right = 0, top = 0, low = 0;
+#pragma unroll
+    for (int i = 15; i >= 1; --i) {
+        if (i < n) {
+            const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+            const unsigned d = v - __popc(right & ((1u << v) - 1u));
+            right |= 1u << v;
+            if (i >= 12) top = top * (unsigned)(i + 1) + d;
+            else low = low * (unsigned)(i + 1) + d;
+        }
+    }
+    return (uint64_t)top * fact(12) + low;
+}
+
+// Inverse of pos_rank: from the top position down, position i holds the d_i-th smallest of the
+// values not yet placed.  The unplaced values are kept sorted in the nibbles of `avail`.
+__device__ __forceinline__ uint64_t pos_unrank(uint64_t r, int n) {
+    unsigned top = 0, low = (unsigned)r;
+    if (n > 12) {
+        top = (unsigned)(r / fact(12));
+        low = (unsigned)(r - (uint64_t)top * fact(12));
+    }
+    uint64_t avail = 0xFEDCBA9876543210ull;
+    uint64_t key = 0;
+#pragma unroll
+    for (int i = 15; i >= 1; --i) {
+        if (i < n) {
+            unsigned d;
+            if (i >= 12) {
+                const unsigned w = (unsigned)(fact(i) / fact(12));
+                d = top / w;
+                top -= d * w;
+            } else {
+                const unsigned w = (unsigned)fact(i);
+                d = low / w;
+                low -= d * w;
+            }
+            const unsigned sh = 4u * d;
+            const uint64_t below = (1ull << sh) - 1ull;
+            key |= ((avail >> sh) & 15ull) << (4 * i);
+            avail = (avail & below) | ((avail >> 4) & ~below);
+        }
+    }
+    return key | (avail & 15ull);
+}
+
+// Append block index b (lanes with `want`) to the warp's staging buffer; flush to the global
+// list with one atomic when it holds at least 32 entries.
+__device__ __forceinline__ void list_stage(unsigned* buf, int& cnt, bool want, unsigned b,
+                                           unsigned* list, unsigned long long* lcount, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (want) buf[cnt + __popc(m & lanemask_lt())] = b;
+    cnt += __popc(m);
+    __syncwarp();
+    if (cnt >= kListStage - 32) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(lcount, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < cnt; i += 32) list[base + i] = buf[i];
+        cnt = 0;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void list_flush(unsigned* buf, int& cnt, unsigned* list,
+                                           unsigned long long* lcount, int lane) {
+    if (cnt == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(lcount, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < cnt; i += 32) list[base + i] = buf[i];
+    cnt = 0;
+    __syncwarp();
+}
+
+// Expand one state (lanes with `active`): apply every generator, test-and-set the images in V,
+// record the new ones in the next layer.
+template <int kILP>
+__device__ __forceinline__ void sweep_state(const GenSM* gens, int k, int n, unsigned* V, unsigned* N,
+                                            unsigned* SN, unsigned* list, unsigned long long* lcount,
+                                            unsigned* lbuf, int& lcnt, bool active, uint64_t rank,
+                                            unsigned& fresh, int lane) {
+    const uint64_t s = active ? pos_unrank(rank, n) : 0;
+    for (int g0 = 0; g0 < k; g0 += kILP) {
+        uint64_t rt[kILP];
+        unsigned old[kILP];
+#pragma unroll
+        for (int i = 0; i < kILP; ++i)
+            if (active && g0 + i < k) rt[i] = pos_rank(apply_gen(gens[g0 + i], s), n);
+#pragma unroll
+        for (int i = 0; i < kILP; ++i)
+            if (active && g0 + i < k) old[i] = atomicOr(V + (rt[i] >> 5), 1u << (unsigned)(rt[i] & 31u));
+#pragma unroll
+        for (int i = 0; i < kILP; ++i) {
+            bool first_in_block = false;
+            unsigned blk = 0;
+            if (active && g0 + i < k) {
+                const unsigned bit = 1u << (unsigned)(rt[i] & 31u);
+                if (!(old[i] & bit)) {
+                    ++fresh;
+                    if (atomicOr(N + (rt[i] >> 5), bit) == 0u) {
+                        blk = (unsigned)(rt[i] >> 10);
+                        const unsigned sb = 1u << (blk & 31u);
+                        first_in_block = !(atomicOr(SN + (blk >> 5), sb) & sb);
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, first_in_block))
+                list_stage(lbuf, lcnt, first_in_block, blk, list, lcount, lane);
+        }
+    }
+}
+
+// Close a round (one thread of the last block to arrive).
+__device__ void sweep_close(SweepDev& D, Ctl* ctl) {
+    volatile SweepDev& W = D;
+    const int r = W.radius;
+    const unsigned long long fresh = ld_relaxed_ull(&D.fresh);
+    if (fresh == 0) {
+        W.status = kDone;
+    } else {
+        const int r1 = r + 1;
+        D.layer_sizes[r1] = fresh;
+        W.radius = r1;
+        if (D.max_radius >= 0 && r1 >= D.max_radius) W.status = kTruncRadius;
+        else if (D.stop_above > 0 && fresh > D.stop_above) W.status = kTruncAbove;
+        else if (r1 + 1 >= D.layers_cap) W.status = kTruncRadius;
+    }
+    // The list of layer r-1 was cleared in this round: it receives layer r+2.
+    W.lcount[(r + 2) % 3] = 0;
+    W.fresh = 0;
+    W.grab = 0;
+    *(volatile int*)&ctl->rounds += 1;
+    __threadfence();
+}
+
+template <int kILP>
+__global__ void __launch_bounds__(kSweepBlock, 4)
+sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
+    __shared__ unsigned short s_off[kSweepWarps][1024];
+    __shared__ uint64_t s_carry[kSweepWarps][32];
+    __shared__ unsigned s_list[kSweepWarps][kListStage];
+    __shared__ GenSM s_gens[kSweepSmemGens];
+    __shared__ unsigned long long s_fresh;
+    SweepDev& D = *Dp;
+    const int k = D.k, n = D.n;
+    const GenSM* gens = D.gens;
+    if (k <= kSweepSmemGens) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) s_gens[j] = D.gens[j];
+        gens = s_gens;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned short* off = s_off[wid];
+    uint64_t* carry = s_carry[wid];
+    unsigned* lbuf = s_list[wid];
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * kSweepWarps;
+
+    for (int round = 0; round < max_rounds; ++round) {
+        if (ld_relaxed_int(&D.status) != kRunning) break;
+        const int r = ld_relaxed_int(&D.radius);
+        const int cur = r % 3, nxt = (r + 1) % 3, prv = (r + 2) % 3;
+        unsigned* F = D.F[cur];
+        unsigned* N = D.F[nxt];
+        unsigned* SN = D.S[nxt];
+        unsigned* P = D.F[prv];
+        unsigned* SP = D.S[prv];
+        const unsigned* Lc = D.L[cur];
+        const unsigned* Lp = D.L[prv];
+        unsigned* Ln = D.L[nxt];
+        unsigned long long* ln_count = &D.lcount[nxt];
+        const unsigned long long ncur = ld_relaxed_ull(&D.lcount[cur]);
+        const unsigned long long nprv = r > 0 ? ld_relaxed_ull(&D.lcount[prv]) : 0ull;
+        const unsigned long long items = ncur + nprv;
+        if (threadIdx.x == 0) s_fresh = 0;
+        __syncthreads();
+
+        // Work units: 32 * |L_r| words of layer r (32 ranks each), then the |L_{r-1}| blocks of
+        // layer r-1 to clear.  A warp fetches 32 units at a time (one per lane) and queues the
+        // ranks of their set bits; it expands them 32 at a time, carrying fewer than 32 over to
+        // the next fetch, so every chunk but the warp's last fills all lanes.
+        const unsigned long long xunits = ncur * 32;
+        const unsigned long long units = xunits + nprv;
+        unsigned fresh = 0;
+        int lcnt = 0;
+        unsigned ncarry = 0, T = 0, i = 0;  // queue: [0, ncarry) in carry, [ncarry, T) in off
+        uint64_t lbase = 0;                 // first rank of this lane's fetched word
+        unsigned long long ua = 0, ub = 0;  // grabbed, not yet fetched units
+        unsigned long long seen = 0;
+        bool exhausted = false;
+        const uint64_t t_round = globaltimer_ns();
+        unsigned guard = 0;
+        for (;;) {
+            // a round that runs past the wait limit is abandoned with an error (never expected:
+            // the loop ends when the round's units are used up)
+            if ((++guard & 1023u) == 0 &&
+                __any_sync(0xffffffffu, globaltimer_ns() - t_round > timeout_ns)) {
+                if (lane == 0) atomicCAS(&ctl->err, 0, CG_ETIMEOUT);
+                break;
+            }
+            if (i + 32 <= T || (exhausted && i < T)) {
+                const unsigned q = i + lane;
+                const bool active = q < T;
+                const unsigned o = (active && q >= ncarry) ? off[q - ncarry] : 0u;
+                const uint64_t b = __shfl_sync(0xffffffffu, lbase, o >> 5);
+                const uint64_t rank = !active ? 0ull : q < ncarry ? carry[q] : b + (o & 31u);
+                sweep_state<kILP>(gens, k, n, D.V, N, SN, Ln, ln_count, lbuf, lcnt, active, rank,
+                                  fresh, lane);
+                i += 32;
+                continue;
+            }
+            if (exhausted) break;
+            {   // keep the queue's remainder (< 32 ranks) in carry
+                const unsigned q = i + lane;
+                const unsigned o = (q < T && q >= ncarry) ? off[q - ncarry] : 0u;
+                const uint64_t b = __shfl_sync(0xffffffffu, lbase, o >> 5);
+                const uint64_t keep = q >= T ? 0ull : q < ncarry ? carry[q] : b + (o & 31u);
+                __syncwarp();
+                if (q < T) carry[lane] = keep;
+                ncarry = T > i ? T - i : 0u;
+                T = ncarry;
+                i = 0;
+                __syncwarp();
+            }
+            if (ua >= ub) {
+                // guided chunk: a quarter of the remaining units' share of one warp, at least 32
+                unsigned long long a = 0, g = 0;
+                if (lane == 0) {
+                    const unsigned long long rem = seen < units ? units - seen : 0;
+                    g = rem / (4 * nwarps);
+                    if (g < 32) g = 32;
+                    a = atomicAdd(&D.grab, g);
+                }
+                a = __shfl_sync(0xffffffffu, a, 0);
+                g = __shfl_sync(0xffffffffu, g, 0);
+                if (a >= units) {
+                    exhausted = true;
+                    continue;
+                }
+                ua = a;
+                ub = a + g < units ? a + g : units;
+                seen = ub;
+            }
+            const unsigned long long u = ua + lane;
+            unsigned fw = 0;
+            lbase = 0;
+            if (u < ub) {
+                if (u < xunits) {
+                    const unsigned blk = __ldcg(Lc + (u >> 5));
+                    const unsigned w = (unsigned)(u & 31u);
+                    fw = __ldcg(F + (uint64_t)blk * 32 + w);
+                    lbase = ((uint64_t)blk << 10) | (w << 5);
+                } else {
+                    // clear a block of layer r-1: its 32 words and its summary word
+                    const unsigned blk = __ldcg(Lp + (u - xunits));
+                    uint4* pw = reinterpret_cast<uint4*>(P + (uint64_t)blk * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) pw[j] = make_uint4(0u, 0u, 0u, 0u);
+                    SP[blk >> 5] = 0u;
+                }
+            }
+            ua = ua + 32 < ub ? ua + 32 : ub;
+            // append the fetched ranks to the queue: offsets (lane << 5 | bit) after the carry
+            const unsigned c = __popc(fw);
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned pos = incl - c;
+            for (unsigned m = fw; m; m &= m - 1) off[pos++] = (unsigned short)((lane << 5) | (__ffs(m) - 1));
+            __syncwarp();
+            T = ncarry + total;
+        }
+        list_flush(lbuf, lcnt, Ln, ln_count, lane);
+        // states found by the block
+#pragma unroll
+        for (int o = 16; o; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+        if (lane == 0 && fresh) atomicAdd(&s_fresh, (unsigned long long)fresh);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_fresh) atomicAdd(&D.fresh, s_fresh);
+
+        const int arrive = grid_arrive(ctl, timeout_ns);
+        if (arrive < 0) return;
+        if (arrive == 1) {
+            if (threadIdx.x == 0) sweep_close(D, ctl);
+            grid_release(ctl);
+        }
+    }
+}
+
+using sweep_fn_t = void (*)(SweepDev*, Ctl*, int, uint64_t);
+
+sweep_fn_t sweep_fn(int ilp) {
+    switch (ilp) {
+        case 1: return sweep_grow_kernel<1>;
+        case 2: return sweep_grow_kernel<2>;
+        case 3: return sweep_grow_kernel<3>;
+        default: return sweep_grow_kernel<4>;
+    }
+}
+
+// Start state: its bit in V and F[0], its block in S[0] and L[0].
+__global__ void sweep_init_kernel(SweepDev* Dp) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    SweepDev& D = *Dp;
+    const uint64_t r = D.start_rank;
+    const unsigned bit = 1u << (unsigned)(r & 31u);
+    const unsigned blk = (unsigned)(r >> 10);
+    D.V[r >> 5] |= bit;
+    D.F[0][r >> 5] |= bit;
+    D.S[0][blk >> 5] |= 1u << (blk & 31u);
+    D.L[0][0] = blk;
+    D.lcount[0] = 1;
+    D.lcount[1] = 0;
+    D.lcount[2] = 0;
+    D.layer_sizes[0] = 1;
+    D.grab = 0;
+    D.fresh = 0;
+    D.radius = 0;
+    D.status = D.max_radius == 0 ? kTruncRadius : kRunning;
+}
+
+// Keys of layer `which` (its bitmap F and block list L[0, nlist)): every set bit unranked and
+// written to out at a position from one counter (order unspecified).  Writes at most cap keys;
+// *count receives the number of states.
+__global__ void sweep_export_kernel(const unsigned* F, const unsigned* L, unsigned long long nlist,
+                                    int n, uint64_t* out, unsigned long long cap,
+                                    unsigned long long* count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long it = w; it < nlist; it += nw) {
+        const unsigned blk = L[it];
+        const unsigned fw = F[(uint64_t)blk * 32 + lane];
+        const unsigned c = __popc(fw);
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0 && total) base = atomicAdd(count, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0) + (incl - c);
+        for (unsigned m = fw; m; m &= m - 1) {
+            const uint64_t rank = ((uint64_t)blk << 10) + lane * 32 + __ffs(m) - 1;
+            if (base < cap) out[base] = pos_unrank(rank, n);
+            ++base;
+        }
+    }
+}
+
+__global__ void pos_rank_kernel(const uint64_t* keys, unsigned long long count, int n, uint64_t* out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        out[i] = pos_rank(keys[i], n);
+}
+
+__global__ void pos_unrank_kernel(const uint64_t* ranks, unsigned long long count, int n, uint64_t* out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        out[i] = pos_unrank(ranks[i], n);
+}
+
+}  // namespace
+
+int sweep_max_grid(int device, int ilp) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn(ilp), kSweepBlock, 0) != cudaSuccess)
+        return -1;
+    return sms * per_sm;
+}
+
+cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st) {
+    sweep_init_kernel<<<1, 32, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
+                              int ilp, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kSweepBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_fn(ilp), d, ctl, max_rounds, timeout_ns);
+}
+
+cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,
+                                uint64_t* out, unsigned long long cap, unsigned long long* count,
+                                int grid, cudaStream_t st) {
+    if (nlist == 0) return cudaSuccess;
+    sweep_export_kernel<<<grid, 256, 0, st>>>(F, L, nlist, n, out, cap, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pos_rank(const uint64_t* keys, unsigned long long count, int n, uint64_t* out,
+                            int grid, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    pos_rank_kernel<<<grid, 256, 0, st>>>(keys, count, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pos_unrank(const uint64_t* ranks, unsigned long long count, int n, uint64_t* out,
+                              int grid, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    pos_unrank_kernel<<<grid, 256, 0, st>>>(ranks, count, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -35,6 +35,7 @@ from .families import (  # noqa: F401
 from .configs import (  # noqa: F401
     BATCH_SEED,
     SERVE_SEED,
+    GrowthJob,
     batch_groups,
     config_s8_coxeter,
     config_s11_lrx,
