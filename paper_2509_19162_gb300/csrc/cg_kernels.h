@@ -33,10 +33,10 @@ cudaError_t launch_hash_insert(uint64_t* table, uint64_t mask, const uint64_t* k
                                int* fail, int grid, cudaStream_t st);
 
 // sweep strategy (sweep_path.cu)
-int sweep_max_grid(int device, int ilp);
+int sweep_max_grid(int device, int ilp, int n);
 cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st);
 cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
-                              int ilp, cudaStream_t st);
+                              int ilp, int n, cudaStream_t st);
 // Unrank the states of one layer (bitmap F, block list L[0, nlist)) into out[0, cap); *count
 // (zeroed by the caller) receives the number of states.
 cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,

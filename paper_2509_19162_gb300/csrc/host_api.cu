@@ -593,7 +593,7 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
     h->stats.h2d_bytes += sizeof(D);
     // two generators in flight per thread measured best (S_12 Coxeter, S_13 pancake)
     const int ilp = h->ilp_override > 0 ? h->ilp_override : std::min(h->k, 2);
-    int grid = cg::sweep_max_grid(h->device, ilp);
+    int grid = cg::sweep_max_grid(h->device, ilp, h->n);
     if (grid <= 0) return CG_ECUDA;
     if (h->grid_override > 0) grid = std::min(grid, h->grid_override);
     if (!h->ev0) {
@@ -602,7 +602,7 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
     }
     if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
     if ((e = cg::launch_sweep_grow(h->d_sweep, h->d_ctl, grid, cg::kMaxLayers + 1, kSweepTimeoutNs, ilp,
-                                   st)) != cudaSuccess)
+                                   h->n, st)) != cudaSuccess)
         return cuda_rc(e);
     if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
     h->stats.launches += 1;

@@ -20,6 +20,7 @@
 //   grid barrier; the last block to arrive records |L_{r+1}| and the stop tests.
 // Units are drawn by warps from one counter in decreasing chunks (guided scheduling).
 #include <cstdio>
+#include <utility>
 
 #include "cg_device.cuh"
 #include "cg_kernels.h"
@@ -35,52 +36,55 @@ constexpr int kListStage = 64;   // staged block-list entries per warp
 
 __host__ __device__ constexpr uint64_t fact(int i) { return i <= 1 ? 1ull : (uint64_t)i * fact(i - 1); }
 
-// rank(s) for a packed permutation of 0..n-1 (element i in bits 4i..4i+3), n <= 16.  Digits are
+// Digit weights of the two halves of the rank, as 32-bit constants: i! for positions below 12,
+// i!/12! for positions 12..15.  Called with unrolled-loop constants, so every division by a
+// weight below is by a compile-time constant.
+__host__ __device__ constexpr unsigned weight_low(int i) { return (unsigned)fact(i); }
+__host__ __device__ constexpr unsigned weight_top(int i) { return (unsigned)(fact(i) / fact(12)); }
+
+// rank(s) for a packed permutation of 0..N-1 (element i in bits 4i..4i+3), N <= 16.  Digits are
 // taken from the top position down: d_i = s_i - #{j > i : s_j < s_i}.  The digits of positions
 // 12.. and 1..11 are combined in two 32-bit Horner sums (both fit), then joined.
-__device__ __forceinline__ uint64_t pos_rank(uint64_t key, int n) {
+template <int N>
+__device__ __forceinline__ uint64_t pos_rank(uint64_t key) {
     unsigned right = 0, top = 0, low = 0;
 #pragma unroll
-    for (int i = 15; i >= 1; --i) {
-        if (i < n) {
-            const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-            const unsigned d = v - __popc(right & ((1u << v) - 1u));
-            right |= 1u << v;
-            if (i >= 12) top = top * (unsigned)(i + 1) + d;
-            else low = low * (unsigned)(i + 1) + d;
-        }
+    for (int i = N - 1; i >= 1; --i) {
+        const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+        const unsigned d = v - __popc(right & ((1u << v) - 1u));
+        right |= 1u << v;
+        if (i >= 12) top = top * (unsigned)(i + 1) + d;
+        else low = low * (unsigned)(i + 1) + d;
     }
-    return (uint64_t)top * fact(12) + low;
+    if (N > 12) return (uint64_t)top * fact(12) + low;
+    return low;
 }
 
 // Inverse of pos_rank: from the top position down, position i holds the d_i-th smallest of the
 // values not yet placed.  The unplaced values are kept sorted in the nibbles of `avail`.
-__device__ __forceinline__ uint64_t pos_unrank(uint64_t r, int n) {
+template <int N>
+__device__ __forceinline__ uint64_t pos_unrank(uint64_t r) {
     unsigned top = 0, low = (unsigned)r;
-    if (n > 12) {
+    if (N > 12) {
         top = (unsigned)(r / fact(12));
         low = (unsigned)(r - (uint64_t)top * fact(12));
     }
     uint64_t avail = 0xFEDCBA9876543210ull;
     uint64_t key = 0;
 #pragma unroll
-    for (int i = 15; i >= 1; --i) {
-        if (i < n) {
-            unsigned d;
-            if (i >= 12) {
-                const unsigned w = (unsigned)(fact(i) / fact(12));
-                d = top / w;
-                top -= d * w;
-            } else {
-                const unsigned w = (unsigned)fact(i);
-                d = low / w;
-                low -= d * w;
-            }
-            const unsigned sh = 4u * d;
-            const uint64_t below = (1ull << sh) - 1ull;
-            key |= ((avail >> sh) & 15ull) << (4 * i);
-            avail = (avail & below) | ((avail >> 4) & ~below);
+    for (int i = N - 1; i >= 1; --i) {
+        unsigned d;
+        if (i >= 12) {
+            d = top / weight_top(i);
+            top -= d * weight_top(i);
+        } else {
+            d = low / weight_low(i);
+            low -= d * weight_low(i);
         }
+        const unsigned sh = 4u * d;
+        const uint64_t below = (1ull << sh) - 1ull;
+        key |= ((avail >> sh) & 15ull) << (4 * i);
+        avail = (avail & below) | ((avail >> 4) & ~below);
     }
     return key | (avail & 15ull);
 }
@@ -116,18 +120,18 @@ __device__ __forceinline__ void list_flush(unsigned* buf, int& cnt, unsigned* li
 
 // Expand one state (lanes with `active`): apply every generator, test-and-set the images in V,
 // record the new ones in the next layer.
-template <int kILP>
-__device__ __forceinline__ void sweep_state(const GenSM* gens, int k, int n, unsigned* V, unsigned* N,
+template <int kILP, int kN>
+__device__ __forceinline__ void sweep_state(const GenSM* gens, int k, unsigned* V, unsigned* N,
                                             unsigned* SN, unsigned* list, unsigned long long* lcount,
                                             unsigned* lbuf, int& lcnt, bool active, uint64_t rank,
                                             unsigned& fresh, int lane) {
-    const uint64_t s = active ? pos_unrank(rank, n) : 0;
+    const uint64_t s = active ? pos_unrank<kN>(rank) : 0;
     for (int g0 = 0; g0 < k; g0 += kILP) {
         uint64_t rt[kILP];
         unsigned old[kILP];
 #pragma unroll
         for (int i = 0; i < kILP; ++i)
-            if (active && g0 + i < k) rt[i] = pos_rank(apply_gen(gens[g0 + i], s), n);
+            if (active && g0 + i < k) rt[i] = pos_rank<kN>(apply_gen(gens[g0 + i], s));
 #pragma unroll
         for (int i = 0; i < kILP; ++i)
             if (active && g0 + i < k) old[i] = atomicOr(V + (rt[i] >> 5), 1u << (unsigned)(rt[i] & 31u));
@@ -175,7 +179,7 @@ __device__ void sweep_close(SweepDev& D, Ctl* ctl) {
     __threadfence();
 }
 
-template <int kILP>
+template <int kILP, int kN>
 __global__ void __launch_bounds__(kSweepBlock, 4)
 sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
     __shared__ unsigned short s_off[kSweepWarps][1024];
@@ -184,7 +188,7 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
     __shared__ GenSM s_gens[kSweepSmemGens];
     __shared__ unsigned long long s_fresh;
     SweepDev& D = *Dp;
-    const int k = D.k, n = D.n;
+    const int k = D.k;
     const GenSM* gens = D.gens;
     if (k <= kSweepSmemGens) {
         for (int j = threadIdx.x; j < k; j += blockDim.x) s_gens[j] = D.gens[j];
@@ -245,8 +249,8 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
                 const unsigned o = (active && q >= ncarry) ? off[q - ncarry] : 0u;
                 const uint64_t b = __shfl_sync(0xffffffffu, lbase, o >> 5);
                 const uint64_t rank = !active ? 0ull : q < ncarry ? carry[q] : b + (o & 31u);
-                sweep_state<kILP>(gens, k, n, D.V, N, SN, Ln, ln_count, lbuf, lcnt, active, rank,
-                                  fresh, lane);
+                sweep_state<kILP, kN>(gens, k, D.V, N, SN, Ln, ln_count, lbuf, lcnt, active, rank,
+                                      fresh, lane);
                 i += 32;
                 continue;
             }
@@ -334,13 +338,19 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
 
 using sweep_fn_t = void (*)(SweepDev*, Ctl*, int, uint64_t);
 
-sweep_fn_t sweep_fn(int ilp) {
-    switch (ilp) {
-        case 1: return sweep_grow_kernel<1>;
-        case 2: return sweep_grow_kernel<2>;
-        case 3: return sweep_grow_kernel<3>;
-        default: return sweep_grow_kernel<4>;
-    }
+// The sweep kernel is compiled for every n (its rank arithmetic unrolls over n) and for one or
+// two generators in flight per thread.
+template <int kILP, int... Ns>
+sweep_fn_t sweep_pick(int n, std::integer_sequence<int, Ns...>) {
+    sweep_fn_t f = nullptr;
+    (void)((n == Ns + 2 ? (f = sweep_grow_kernel<kILP, Ns + 2>, 0) : 0) + ...);
+    return f;
+}
+
+sweep_fn_t sweep_fn(int ilp, int n) {
+    if (n < 2 || n > 14) return nullptr;
+    return ilp <= 1 ? sweep_pick<1>(n, std::make_integer_sequence<int, 13>{})
+                    : sweep_pick<2>(n, std::make_integer_sequence<int, 13>{});
 }
 
 // Start state: its bit in V and F[0], its block in S[0] and L[0].
@@ -367,9 +377,9 @@ __global__ void sweep_init_kernel(SweepDev* Dp) {
 // Keys of layer `which` (its bitmap F and block list L[0, nlist)): every set bit unranked and
 // written to out at a position from one counter (order unspecified).  Writes at most cap keys;
 // *count receives the number of states.
+template <int kN>
 __global__ void sweep_export_kernel(const unsigned* F, const unsigned* L, unsigned long long nlist,
-                                    int n, uint64_t* out, unsigned long long cap,
-                                    unsigned long long* count) {
+                                    uint64_t* out, unsigned long long cap, unsigned long long* count) {
     const int lane = threadIdx.x & 31;
     const unsigned long long w = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -389,30 +399,66 @@ __global__ void sweep_export_kernel(const unsigned* F, const unsigned* L, unsign
         base = __shfl_sync(0xffffffffu, base, 0) + (incl - c);
         for (unsigned m = fw; m; m &= m - 1) {
             const uint64_t rank = ((uint64_t)blk << 10) + lane * 32 + __ffs(m) - 1;
-            if (base < cap) out[base] = pos_unrank(rank, n);
+            if (base < cap) out[base] = pos_unrank<kN>(rank);
             ++base;
         }
     }
 }
 
-__global__ void pos_rank_kernel(const uint64_t* keys, unsigned long long count, int n, uint64_t* out) {
+template <int kN>
+__global__ void pos_rank_kernel(const uint64_t* keys, unsigned long long count, uint64_t* out) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        out[i] = pos_rank(keys[i], n);
+        out[i] = pos_rank<kN>(keys[i]);
 }
 
-__global__ void pos_unrank_kernel(const uint64_t* ranks, unsigned long long count, int n, uint64_t* out) {
+template <int kN>
+__global__ void pos_unrank_kernel(const uint64_t* ranks, unsigned long long count, uint64_t* out) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        out[i] = pos_unrank(ranks[i], n);
+        out[i] = pos_unrank<kN>(ranks[i]);
 }
+
+// Launch K<n> for a runtime n in 1..16 with the given arguments.
+template <template <int> class K, int... Ns, typename... A>
+cudaError_t launch_by_n_impl(std::integer_sequence<int, Ns...>, int n, int grid, cudaStream_t st,
+                             A... args) {
+    cudaError_t e = cudaErrorInvalidValue;
+    (void)((n == Ns + 1 ? (K<Ns + 1>::launch(grid, st, args...), e = cudaGetLastError(), 0) : 0) + ...);
+    return e;
+}
+
+template <template <int> class K, typename... A>
+cudaError_t launch_by_n(int n, int grid, cudaStream_t st, A... args) {
+    return launch_by_n_impl<K>(std::make_integer_sequence<int, 16>{}, n, grid, st, args...);
+}
+
+template <int kN> struct RankK {
+    static void launch(int grid, cudaStream_t st, const uint64_t* a, unsigned long long c, uint64_t* o) {
+        pos_rank_kernel<kN><<<grid, 256, 0, st>>>(a, c, o);
+    }
+};
+template <int kN> struct UnrankK {
+    static void launch(int grid, cudaStream_t st, const uint64_t* a, unsigned long long c, uint64_t* o) {
+        pos_unrank_kernel<kN><<<grid, 256, 0, st>>>(a, c, o);
+    }
+};
+template <int kN> struct ExportK {
+    static void launch(int grid, cudaStream_t st, const unsigned* F, const unsigned* L,
+                       unsigned long long nl, uint64_t* out, unsigned long long cap,
+                       unsigned long long* count) {
+        sweep_export_kernel<kN><<<grid, 256, 0, st>>>(F, L, nl, out, cap, count);
+    }
+};
 
 }  // namespace
 
-int sweep_max_grid(int device, int ilp) {
+int sweep_max_grid(int device, int ilp, int n) {
     int sms = 0, per_sm = 0;
+    const sweep_fn_t f = sweep_fn(ilp, n);
+    if (!f) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn(ilp), kSweepBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kSweepBlock, 0) != cudaSuccess)
         return -1;
     return sms * per_sm;
 }
@@ -423,7 +469,9 @@ cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st) {
 }
 
 cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
-                              int ilp, cudaStream_t st) {
+                              int ilp, int n, cudaStream_t st) {
+    const sweep_fn_t f = sweep_fn(ilp, n);
+    if (!f) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kSweepBlock);
@@ -434,29 +482,26 @@ cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, u
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_fn(ilp), d, ctl, max_rounds, timeout_ns);
+    return cudaLaunchKernelEx(&cfg, f, d, ctl, max_rounds, timeout_ns);
 }
 
 cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,
                                 uint64_t* out, unsigned long long cap, unsigned long long* count,
                                 int grid, cudaStream_t st) {
     if (nlist == 0) return cudaSuccess;
-    sweep_export_kernel<<<grid, 256, 0, st>>>(F, L, nlist, n, out, cap, count);
-    return cudaGetLastError();
+    return launch_by_n<ExportK>(n, grid, st, F, L, nlist, out, cap, count);
 }
 
 cudaError_t launch_pos_rank(const uint64_t* keys, unsigned long long count, int n, uint64_t* out,
                             int grid, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    pos_rank_kernel<<<grid, 256, 0, st>>>(keys, count, n, out);
-    return cudaGetLastError();
+    return launch_by_n<RankK>(n, grid, st, keys, count, out);
 }
 
 cudaError_t launch_pos_unrank(const uint64_t* ranks, unsigned long long count, int n, uint64_t* out,
                               int grid, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    pos_unrank_kernel<<<grid, 256, 0, st>>>(ranks, count, n, out);
-    return cudaGetLastError();
+    return launch_by_n<UnrankK>(n, grid, st, ranks, count, out);
 }
 
 }  // namespace cg
