@@ -402,7 +402,15 @@ def run_batch(args):
     spec = [(j.n, j.gens, j.inverse_closed, -1) for j in jobs]
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-    batch = cg.Batch(spec)
+    tuned = None
+    if not args.no_autotune:
+        # launch settings picked by the autotuner on this batch (outside the timed region)
+        from paper_2509_19162_gb300 import tune
+        t0 = time.perf_counter()
+        table = tune.TuneTable(args.tune_table) if args.tune_table else None
+        tuned = tune.tune_batch(spec, stream=stream, table=table)
+        tuned["tuning_s"] = time.perf_counter() - t0
+    batch = cg.Batch(spec, **(tuned["options"] if tuned else {}))
     res = None
     for _ in range(args.warmup):
         res = batch.run(stream)
@@ -469,6 +477,10 @@ def run_batch(args):
                    "neighbours_per_step": nb_step, "jobs_per_s": jobs_per_s,
                    "one_at_a_time_jobs_per_s": len(sample) / one_s,
                    "batched_over_one_at_a_time": jobs_per_s / (len(sample) / one_s),
+                   "autotune": None if not tuned else {
+                       "settings": tuned["settings"], "tuned_ms": tuned["seconds"] * 1e3,
+                       "default_ms": tuned["default_seconds"] * 1e3, "trials": tuned["trials"],
+                       "tuning_s": tuned["tuning_s"]},
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "groups sharded over ranks" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -554,6 +566,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--strategy", default="auto", choices=["auto", "hash", "bitmap", "sort", "sweep"],
                     help="visited-set strategy of the single-job workloads")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch workload: run with the library's default launch settings")
+    ap.add_argument("--tune-table", default=None, help="JSON file to record tuned settings in")
     ap.add_argument("--serve-jobs", type=int, default=20000)
     ap.add_argument("--serve-job-mem", type=int, default=64, help="per-job device memory cap, MiB")
     ap.add_argument("--serve-slots", type=int, default=512)

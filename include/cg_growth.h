@@ -74,6 +74,15 @@ extern "C" {
                                   together, probing one slot per step; 9..12: the same with
                                   ILP = value - 8, probing a whole 32-byte sector per step;
                                   0: library chooses                                          */
+/* batch options (cg_batch_set_option; CG_OPT_ILP and CG_OPT_GRID apply there too, 1..4)      */
+#define CG_OPT_BATCH_WAVE_L2 6 /* cap on the summed visited-set bytes of one launch:
+                                  0 = half of L2 (default), -1 = none                          */
+#define CG_OPT_BATCH_VISITED 7 /* CG_STRATEGY_AUTO (rank bitmap for dense groups of n <= 12),
+                                  CG_STRATEGY_HASH (hash tables only) or CG_STRATEGY_BITMAP
+                                  (rank bitmap whenever n <= 12 and it fits)                   */
+#define CG_OPT_GRAPH         8 /* 1: when the batch's buffers stay allocated between runs,
+                                  capture a whole run as a CUDA graph at its first run and
+                                  replay it afterwards                                         */
 
 /* ---- device memory ------------------------------------------------------------------ */
 /*
@@ -170,6 +179,11 @@ int cg_growth_destroy(cg_growth_t h);
 /* Human-readable name of a return code (static string). */
 const char* cg_strerror(int code);
 
+/* Name of the last CUDA error that a call on this thread reported as CG_ECUDA or CG_ENOMEM,
+ * with the library source line that saw it ("" if none); valid until the next call on this
+ * thread. */
+const char* cg_last_error_detail(void);
+
 /* ---- batched growth of many independent jobs ------------------------------------------ */
 typedef struct cg_batch* cg_batch_t;
 
@@ -206,6 +220,14 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
  * paper grows one graph at a time.  Errors: CG_EINVAL.
  */
 int cg_batch_set_wave_l2(cg_batch_t b, uint64_t bytes);
+
+/*
+ * Set a batch option (CG_OPT_ILP, CG_OPT_GRID, CG_OPT_BATCH_WAVE_L2, CG_OPT_BATCH_VISITED,
+ * CG_OPT_GRAPH) before cg_batch_run.  The batch is planned at its first run: visited-set kind per
+ * job, waves, and, when every wave fits mem_cap together, device buffers kept between runs.
+ * Changing an option (other than CG_OPT_GRAPH) drops the plan.  Errors: CG_EINVAL.
+ */
+int cg_batch_set_option(cg_batch_t b, int option, int64_t value);
 
 /* Measurements of the last cg_batch_run (as cg_growth_get_stats).  Errors: CG_EINVAL. */
 int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out);

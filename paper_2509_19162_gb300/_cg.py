@@ -29,6 +29,9 @@ CG_STRATEGY_HASH = 1
 CG_STRATEGY_SORT = 2
 CG_STRATEGY_BITMAP = 3
 CG_STRATEGY_SWEEP = 4
+CG_OPT_BATCH_WAVE_L2 = 6
+CG_OPT_BATCH_VISITED = 7
+CG_OPT_GRAPH = 8
 
 CG_OPT_STRATEGY = 1
 CG_OPT_STOP_ABOVE = 2
@@ -63,12 +66,14 @@ SIGNATURES = {
     "cg_growth_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(cg_growth_stats)]),
     "cg_growth_destroy": (ctypes.c_int, [_vp]),
     "cg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "cg_last_error_detail": (ctypes.c_char_p, []),
     "cg_batch_create": (ctypes.c_int, [ctypes.c_int, _ip, _ip, _u8p, _u64p, _ip, _ip, ctypes.c_uint64,
                                        ctypes.POINTER(_vp)]),
     "cg_batch_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip, _ip]),
     "cg_batch_destroy": (ctypes.c_int, [_vp]),
     "cg_batch_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(cg_growth_stats)]),
     "cg_batch_set_wave_l2": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "cg_batch_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "cg_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.POINTER(_vp)]),
     "cg_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int, _u64p]),
@@ -110,7 +115,8 @@ lib = _load()
 class CgError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} (code {code})")
+        detail = lib.cg_last_error_detail().decode() if code in (-3, -4) else ""
+        super().__init__(f"{where}: {strerror(code)} (code {code})" + (f" [{detail}]" if detail else ""))
 
 
 def strerror(code: int) -> str:
@@ -138,11 +144,13 @@ cg_growth_group_order = _export("cg_growth_group_order")
 cg_growth_get_stats = _export("cg_growth_get_stats")
 cg_growth_destroy = _export("cg_growth_destroy")
 cg_strerror = _export("cg_strerror")
+cg_last_error_detail = _export("cg_last_error_detail")
 cg_batch_create = _export("cg_batch_create")
 cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")
 cg_batch_get_stats = _export("cg_batch_get_stats")
 cg_batch_set_wave_l2 = _export("cg_batch_set_wave_l2")
+cg_batch_set_option = _export("cg_batch_set_option")
 cg_perm_rank = _export("cg_perm_rank")
 cg_perm_unrank = _export("cg_perm_unrank")
 cg_server_create = _export("cg_server_create")

@@ -210,9 +210,14 @@ def growth(n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool]
 class Batch:
     """Many independent growth jobs run together (cg_batch_create ... cg_batch_destroy)."""
 
-    def __init__(self, jobs, mem_cap: int = 0, wave_l2: Optional[int] = None):
-        """jobs: sequence of (n, gens, inverse_closed, max_radius).  wave_l2: cap on the summed
-        visited-set bytes grown in one launch (None: half of L2; -1: no cap)."""
+    VISITED = {"auto": _cg.CG_STRATEGY_AUTO, "hash": _cg.CG_STRATEGY_HASH, "bitmap": _cg.CG_STRATEGY_BITMAP}
+
+    def __init__(self, jobs, mem_cap: int = 0, wave_l2: Optional[int] = None, ilp: int = 0,
+                 grid: int = 0, visited: str = "auto", graph: bool = False):
+        """jobs: sequence of (n, gens, inverse_closed, max_radius).
+        wave_l2: cap on the summed visited-set bytes grown in one launch (None or 0: half of L2;
+        -1: no cap).  ilp, grid: kernel variant and blocks of the launches (0: library choice).
+        visited: "auto", "hash" or "bitmap".  graph: capture a whole run as a CUDA graph."""
         self.njobs = len(jobs)
         ns = np.array([j[0] for j in jobs], dtype=np.int32)
         ks = np.array([len(j[1]) for j in jobs], dtype=np.int32)
@@ -232,14 +237,33 @@ class Batch:
                                       inv.ctypes.data_as(ip), rad.ctypes.data_as(ip), int(mem_cap),
                                       ctypes.byref(h)), "cg_batch_create")
         self._h = h
+        self._out = None
+        self.set_options(wave_l2=wave_l2 or 0, ilp=ilp, grid=grid, visited=visited, graph=graph)
+
+    def set_options(self, wave_l2: Optional[int] = None, ilp: Optional[int] = None,
+                    grid: Optional[int] = None, visited: Optional[str] = None,
+                    graph: Optional[bool] = None) -> None:
+        """Change launch settings (None: unchanged); see __init__."""
+        opts = []
         if wave_l2 is not None:
-            self.set_wave_l2(wave_l2)
+            opts.append((_cg.CG_OPT_BATCH_WAVE_L2, int(wave_l2)))
+        if ilp is not None:
+            opts.append((_cg.CG_OPT_ILP, int(ilp)))
+        if grid is not None:
+            opts.append((_cg.CG_OPT_GRID, int(grid)))
+        if visited is not None:
+            if visited not in self.VISITED:
+                raise ValueError(f"visited must be one of {sorted(self.VISITED)}")
+            opts.append((_cg.CG_OPT_BATCH_VISITED, self.VISITED[visited]))
+        if graph is not None:
+            opts.append((_cg.CG_OPT_GRAPH, int(bool(graph))))
+        for o, v in opts:
+            _cg.check(_cg.cg_batch_set_option(self._h, o, v), "cg_batch_set_option")
 
     def set_wave_l2(self, nbytes: int) -> None:
         """Cap on the summed visited-set bytes of the jobs grown in one launch (0: half of L2,
         -1: no cap)."""
-        v = (1 << 64) - 1 if nbytes < 0 else int(nbytes)
-        _cg.check(_cg.cg_batch_set_wave_l2(self._h, v), "cg_batch_set_wave_l2")
+        self.set_options(wave_l2=nbytes)
 
     def stats(self) -> dict:
         st = _cg.cg_growth_stats()
@@ -247,18 +271,18 @@ class Batch:
         return {f: getattr(st, f) for f, _ in st._fields_}
 
     def run(self, stream=None, cap: int = 512) -> List[GrowthResult]:
-        out = np.zeros(self.njobs * cap, dtype=np.uint64)
-        nl = np.zeros(self.njobs, dtype=np.int32)
-        stv = np.zeros(self.njobs, dtype=np.int32)
+        if self._out is None or self._out[0].shape[1] != cap:
+            self._out = (np.zeros((self.njobs, cap), dtype=np.uint64), np.zeros(self.njobs, dtype=np.int32),
+                         np.zeros(self.njobs, dtype=np.int32))
+        out, nl, stv = self._out
         ip = ctypes.POINTER(ctypes.c_int)
         rc = _cg.cg_batch_run(self._h, _stream_handle(stream),
                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
                               nl.ctypes.data_as(ip), stv.ctypes.data_as(ip))
         _cg.check(rc, "cg_batch_run")
-        res = []
-        for j in range(self.njobs):
-            res.append(GrowthResult([int(x) for x in out[j * cap: j * cap + nl[j]]], int(stv[j])))
-        return res
+        nls = nl.tolist()
+        sts = stv.tolist()
+        return [GrowthResult(out[j, :nls[j]].tolist(), sts[j]) for j in range(self.njobs)]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

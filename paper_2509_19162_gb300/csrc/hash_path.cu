@@ -534,6 +534,7 @@ int hash_grow_max_grid(int device, int ilp, bool multi) {
 
 cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              cudaStream_t st, int only_fresh) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     init_jobs_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(d_jobs, njobs, only_fresh);
     init_units_kernel<<<1, 1, 0, st>>>(d_jobs, njobs, d_ubeg, d_ctl);
     return cudaGetLastError();
@@ -541,12 +542,14 @@ cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ub
 
 cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                                 cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     init_units_kernel<<<1, 1, 0, st>>>(d_jobs, njobs, d_ubeg, d_ctl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              int grid, int max_rounds, uint64_t timeout_ns, int ilp, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kGrowBlock);
@@ -564,6 +567,7 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,
                                  uint64_t mask, uint64_t key_mask, int* d_err, int grid,
                                  cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (count == 0) return cudaSuccess;
     rebuild_table_kernel<<<grid, 256, 0, st>>>(keys, count, table, mask, key_mask, d_err);
     return cudaGetLastError();
@@ -571,6 +575,7 @@ cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count,
 
 cudaError_t launch_rebuild_bitmap(const uint64_t* keys, unsigned long long count, unsigned* bm,
                                   uint64_t words, int n, int* d_err, int grid, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (count == 0) return cudaSuccess;
     rebuild_bitmap_kernel<<<grid, 256, 0, st>>>(keys, count, bm, words, n, d_err);
     return cudaGetLastError();
@@ -578,6 +583,7 @@ cudaError_t launch_rebuild_bitmap(const uint64_t* keys, unsigned long long count
 
 cudaError_t launch_expand(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,
                           uint64_t* out, int grid, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (F == 0) return cudaSuccess;
     expand_kernel<<<grid, 256, 0, st>>>(d_gens, k, in, F, out);
     return cudaGetLastError();
@@ -586,6 +592,7 @@ cudaError_t launch_expand(const GenSM* d_gens, int k, const uint64_t* in, unsign
 cudaError_t launch_hash_insert(uint64_t* table, uint64_t mask, const uint64_t* keys,
                                unsigned long long N, uint64_t* out, unsigned long long* count,
                                int* fail, int grid, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     hash_insert_kernel<<<grid, 256, 0, st>>>(table, mask, keys, N, out, count, fail);
     finish_insert_count_kernel<<<1, 1, 0, st>>>(count, fail);
     return cudaGetLastError();

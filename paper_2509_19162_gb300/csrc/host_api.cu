@@ -217,10 +217,30 @@ uint64_t max_cap_for_mem(uint64_t mem) {
     return best;
 }
 
-int cuda_rc(cudaError_t e) {
+// The last CUDA error this thread turned into a return code, and the source line that did
+// (cg_last_error_detail).
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+thread_local int g_last_cuda_line = 0;
+thread_local char g_last_detail[96];
+
+int cuda_rc_at(cudaError_t e, int line) {
     if (e == cudaSuccess) return CG_OK;
+    g_last_cuda_error = e;
+    g_last_cuda_line = line;
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA;
+}
+#define cuda_rc(e) cuda_rc_at((e), __LINE__)
+
+// Milliseconds between two recorded events, 0 if they cannot be compared; a failed query must
+// not stay pending as this thread's last error (the next launch check would report it).
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
 }
 
 int status_to_rc(int status) {
@@ -479,8 +499,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
             return cuda_rc(e);
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
         h->stats.d2h_bytes += sizeof(J) + sizeof(ctl);
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->stats.kernel_ms += ms;
+        h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
         h->stats.rounds += ctl.rounds;
         if (ctl.err) return ctl.err;
         if (J.status != cg::kNeedMem) break;
@@ -613,8 +632,7 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
         return cuda_rc(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
     h->stats.d2h_bytes += sizeof(D) + sizeof(ctl);
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->stats.kernel_ms += ms;
+    h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
     h->stats.rounds += ctl.rounds;
     if (ctl.err) return ctl.err;
     h->stats.state_capacity = factorial(h->n);
@@ -726,8 +744,7 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
         if ((e = cudaMemcpyAsync(&derr, sc.err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
         h->stats.d2h_bytes += 12;
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->stats.kernel_ms += ms;
+        h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
         h->stats.rounds += 1;
         if (derr) return derr;
         if (Fn == 0) { status = cg::kDone; break; }
@@ -948,6 +965,13 @@ int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64
 
 uint64_t cg_growth_group_order(cg_growth_t h) { return h ? h->order : 0; }
 
+const char* cg_last_error_detail(void) {
+    if (g_last_cuda_error == cudaSuccess) return "";
+    std::snprintf(g_last_detail, sizeof(g_last_detail), "%s at host_api.cu:%d",
+                  cudaGetErrorName(g_last_cuda_error), g_last_cuda_line);
+    return g_last_detail;
+}
+
 int cg_growth_get_stats(cg_growth_t h, cg_growth_stats* out) {
     if (!h || !out) return CG_EINVAL;
     *out = h->stats;
@@ -1084,6 +1108,12 @@ int cg_hash_insert(uint64_t* table, uint64_t slots, const uint64_t* keys, uint64
 }  // extern "C"
 
 // ---- batch of independent jobs ----------------------------------------------------------------
+// The jobs are planned into launches ("waves") once: visited-set kind per job, waves within the
+// memory budget and the L2 cap, one device buffer per wave with the jobs' static descriptors
+// uploaded.  When all waves fit the budget together the buffers stay allocated between runs and
+// a run is a fixed sequence per wave -- clear the visited sets, initialise the jobs, one
+// persistent launch, copy the results to pinned host memory -- which CG_OPT_GRAPH captures once
+// as a CUDA graph and replays.
 struct cg_batch {
     struct Job {
         int n = 0, k = 0, max_radius = -1;
@@ -1092,61 +1122,109 @@ struct cg_batch {
         uint64_t cap = 1;          // states the job may store
         int mode = cg::kVisitHash; // rank bitmap for small dense groups, else hash table
     };
+    struct Wave {
+        std::vector<int> ids;
+        char* base = nullptr;      // resident plans: the wave's device buffer
+        uint64_t bytes = 0;
+        uint64_t o_gens = 0, o_jobs = 0, o_ubeg = 0, o_ctl = 0, o_lay = 0, o_keys = 0, o_tab = 0;
+        std::vector<uint64_t> slots;             // visited-set 8-byte slots per job
+        std::vector<std::pair<uint64_t, uint64_t>> clear_runs[2];  // (offset, bytes): 0 -> 0x00, 1 -> 0xFF
+        std::vector<GenSM> hg;
+        std::vector<JobDev> hj;
+        uint64_t h_off = 0;        // this wave's results in the pinned host buffer
+    };
     std::vector<Job> jobs;
     uint64_t mem_cap = kDefaultMemCap;
     uint64_t wave_l2 = 0;          // cap on summed visited-set bytes per launch; 0: L2 / 2
+    int ilp_override = 0;          // CG_OPT_ILP
+    int grid_override = 0;         // CG_OPT_GRID
+    int visited = 0;               // CG_OPT_BATCH_VISITED
+    int use_graph = 0;             // CG_OPT_GRAPH (-1 after a failed capture)
     cg_growth_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // the plan, rebuilt when an option or the layer capacity changes
+    bool planned = false;
+    int plan_cap = 0;
+    int ilp = 1, grid = 0, device = -1;
+    bool resident = false;
+    std::vector<Wave> waves;
+    char* h_pinned = nullptr;
+    uint64_t h_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;  // stream the graph was captured on
+
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+    }
+    void release() {
+        drop_graph();
+        for (auto& w : waves)
+            if (w.base) dev_free(w.base, nullptr);
+        waves.clear();
+        if (h_pinned) cudaFreeHost(h_pinned);
+        h_pinned = nullptr;
+        h_bytes = 0;
+        planned = false;
+        resident = false;
+        cudaStreamSynchronize(nullptr);
+    }
 };
 
 namespace {
 
-struct BatchBuffers {
-    void* block = nullptr;
-};
+uint64_t al256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
-// Run jobs [first, last) of b in one persistent launch.  Writes layer sizes and statuses.
-int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t* layer_out,
-             int cap, int* nl_out, int* status_out, int grid, int ilp) {
-    const int nj = (int)ids.size();
-    if (nj == 0) return CG_OK;
-    // layout: gens | jobs | ubeg | layers | keys | tables   (each 256-byte aligned)
-    auto al = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+// Lay out one wave's buffer: gens | jobs | ubeg | ctl | layers | keys | tables.
+void layout_wave(cg_batch* b, cg_batch::Wave& w, int lcap) {
+    const int nj = (int)w.ids.size();
     uint64_t ngens = 0, nkeys = 0, nslots = 0;
-    std::vector<uint64_t> goff(nj), koff(nj), toff(nj), slots(nj);
+    std::vector<uint64_t> goff(nj), koff(nj), toff(nj);
+    w.slots.assign(nj, 0);
     for (int i = 0; i < nj; ++i) {
-        const auto& J = b->jobs[ids[i]];
+        const auto& J = b->jobs[w.ids[i]];
         goff[i] = ngens; ngens += J.gsm.size();
         koff[i] = nkeys; nkeys += J.cap;
-        slots[i] = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) / 2 : table_slots_for(J.cap);
-        toff[i] = nslots; nslots += slots[i];
+        w.slots[i] = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) / 2 : table_slots_for(J.cap);
+        toff[i] = nslots; nslots += w.slots[i];
     }
-    const int lcap = cap + 1;
-    const uint64_t o_gens = 0;
-    const uint64_t o_jobs = al(o_gens + ngens * sizeof(GenSM));
-    const uint64_t o_ubeg = al(o_jobs + nj * sizeof(JobDev));
-    const uint64_t o_ctl = al(o_ubeg + (nj + 1) * 8);
-    const uint64_t o_lay = al(o_ctl + sizeof(Ctl));
-    const uint64_t o_keys = al(o_lay + (uint64_t)nj * lcap * 8);
-    const uint64_t o_tab = al(o_keys + nkeys * 8);
-    const uint64_t total = al(o_tab + nslots * 8);
-    char* base = (char*)dev_alloc(total, st);
-    if (!base) return CG_ENOMEM;
-    int rc = CG_OK;
-    std::vector<GenSM> hg;
-    hg.reserve(ngens);
-    std::vector<JobDev> hj(nj);
+    w.o_gens = 0;
+    w.o_jobs = al256(w.o_gens + ngens * sizeof(GenSM));
+    w.o_ubeg = al256(w.o_jobs + nj * sizeof(JobDev));
+    w.o_ctl = al256(w.o_ubeg + (nj + 1) * 8);
+    w.o_lay = al256(w.o_ctl + sizeof(Ctl));
+    w.o_keys = al256(w.o_lay + (uint64_t)nj * lcap * 8);
+    w.o_tab = al256(w.o_keys + nkeys * 8);
+    w.bytes = al256(w.o_tab + nslots * 8);
+    // visited sets: bitmaps start all-zero, hash tables all-ones; runs of one kind, one memset each
+    for (auto& r : w.clear_runs) r.clear();
+    for (int i = 0; i < nj;) {
+        const int mode = b->jobs[w.ids[i]].mode;
+        int j = i;
+        uint64_t cnt = 0;
+        while (j < nj && b->jobs[w.ids[j]].mode == mode) cnt += w.slots[j++];
+        w.clear_runs[mode == cg::kVisitBitmap ? 0 : 1].push_back({w.o_tab + toff[i] * 8, cnt * 8});
+        i = j;
+    }
+    // static descriptors (pointers filled in by bind_wave)
+    w.hg.clear();
+    w.hg.reserve(ngens);
+    w.hj.assign(nj, JobDev{});
     for (int i = 0; i < nj; ++i) {
-        const auto& J = b->jobs[ids[i]];
-        hg.insert(hg.end(), J.gsm.begin(), J.gsm.end());
-        JobDev& D = hj[i];
+        const auto& J = b->jobs[w.ids[i]];
+        w.hg.insert(w.hg.end(), J.gsm.begin(), J.gsm.end());
+        JobDev& D = w.hj[i];
         std::memset(&D, 0, sizeof(D));
-        D.keys = (uint64_t*)(base + o_keys) + koff[i];
+        D.keys = reinterpret_cast<uint64_t*>(koff[i] * 8);       // offsets until bound
         D.keys_cap = J.cap;
-        D.table = (uint64_t*)(base + o_tab) + toff[i];
-        D.table_mask = slots[i] - 1;
-        D.gens = (const GenSM*)(base + o_gens) + goff[i];
-        D.layer_sizes = (uint64_t*)(base + o_lay) + (uint64_t)i * lcap;
+        D.table = reinterpret_cast<uint64_t*>(toff[i] * 8);
+        D.table_mask = w.slots[i] - 1;
+        D.gens = reinterpret_cast<const GenSM*>(goff[i] * sizeof(GenSM));
+        D.layer_sizes = reinterpret_cast<uint64_t*>((uint64_t)i * lcap * 8);
         D.k = J.k;
         D.n = J.n;
         D.layers_cap = lcap;
@@ -1154,60 +1232,182 @@ int run_wave(cg_batch* b, const std::vector<int>& ids, cudaStream_t st, uint64_t
         D.mode = J.mode;
         D.bitmap_words = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) : 0;
     }
-    JobDev* d_jobs = (JobDev*)(base + o_jobs);
-    unsigned long long* d_ubeg = (unsigned long long*)(base + o_ubeg);
-    Ctl* d_ctl = (Ctl*)(base + o_ctl);
-    cudaError_t e = cudaSuccess;
-    if (ngens) e = cudaMemcpyAsync(base + o_gens, hg.data(), ngens * sizeof(GenSM), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, hj.data(), nj * sizeof(JobDev), cudaMemcpyHostToDevice, st);
-    // visited sets: bitmaps start all-zero, hash tables all-ones (empty marker); runs of jobs of
-    // one kind are filled with one memset each
-    for (int i = 0; i < nj && e == cudaSuccess;) {
-        const int mode = b->jobs[ids[i]].mode;
-        int j = i;
-        uint64_t cnt = 0;
-        while (j < nj && b->jobs[ids[j]].mode == mode) cnt += slots[j++];
-        e = cudaMemsetAsync(base + o_tab + toff[i] * 8, mode == cg::kVisitBitmap ? 0 : 0xFF, cnt * 8, st);
-        i = j;
+}
+
+// Turn the offsets of the wave's descriptors into device addresses of `base` and upload the
+// static part (generators and descriptors).
+cudaError_t bind_wave(cg_batch::Wave& w, char* base, cudaStream_t st) {
+    std::vector<JobDev> hj = w.hj;
+    for (auto& D : hj) {
+        D.keys = reinterpret_cast<uint64_t*>(base + w.o_keys + reinterpret_cast<uint64_t>(D.keys));
+        D.table = reinterpret_cast<uint64_t*>(base + w.o_tab + reinterpret_cast<uint64_t>(D.table));
+        D.gens = reinterpret_cast<const GenSM*>(base + w.o_gens + reinterpret_cast<uint64_t>(D.gens));
+        D.layer_sizes = reinterpret_cast<uint64_t*>(base + w.o_lay + reinterpret_cast<uint64_t>(D.layer_sizes));
     }
+    cudaError_t e = cudaSuccess;
+    if (!w.hg.empty()) e = cudaMemcpyAsync(base + w.o_gens, w.hg.data(), w.hg.size() * sizeof(GenSM),
+                                           cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + w.o_jobs, hj.data(), hj.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // hj is a local copy
+    return e;
+}
+
+// Results of one wave in host memory: descriptors, control block, layer sizes.
+uint64_t wave_result_bytes(const cg_batch::Wave& w, int lcap) {
+    return al256(w.ids.size() * sizeof(JobDev)) + al256(sizeof(Ctl)) + (uint64_t)w.ids.size() * lcap * 8;
+}
+
+// Enqueue one run of a bound wave: clear, initialise, grow, copy results to host memory `hout`.
+cudaError_t enqueue_wave(cg_batch* b, cg_batch::Wave& w, char* base, char* hout, int lcap, cudaStream_t st) {
+    const int nj = (int)w.ids.size();
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v)
+        for (auto& r : w.clear_runs[v]) {
+            e = cudaMemsetAsync(base + r.first, v ? 0xFF : 0, r.second, st);
+            if (e != cudaSuccess) break;
+        }
+    JobDev* d_jobs = reinterpret_cast<JobDev*>(base + w.o_jobs);
+    unsigned long long* d_ubeg = reinterpret_cast<unsigned long long*>(base + w.o_ubeg);
+    Ctl* d_ctl = reinterpret_cast<Ctl*>(base + w.o_ctl);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
-    if (e == cudaSuccess && !b->ev0) e = cudaEventCreate(&b->ev0);
-    if (e == cudaSuccess && !b->ev1) e = cudaEventCreate(&b->ev1);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev0, st);
     if (e == cudaSuccess)
-        e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, grid, lcap + 1, kTimeoutNs, ilp, st);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev1, st);
-    b->stats.launches += 3;
-    b->stats.h2d_bytes += ngens * sizeof(GenSM) + nj * sizeof(JobDev);
-    b->stats.d2h_bytes += nj * sizeof(JobDev) + sizeof(Ctl) + (uint64_t)nj * lcap * 8;
-    Ctl ctl;
-    std::memset(&ctl, 0, sizeof(ctl));
-    std::vector<uint64_t> lay((uint64_t)nj * lcap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hj.data(), d_jobs, nj * sizeof(JobDev), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(lay.data(), base + o_lay, lay.size() * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    float ms = 0.f;
-    if (e == cudaSuccess && cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->stats.kernel_ms += ms;
-    b->stats.rounds += ctl.rounds;
-    if (e != cudaSuccess) rc = cuda_rc(e);
-    else if (ctl.err) rc = ctl.err;
-    if (rc == CG_OK) {
-        for (int i = 0; i < nj; ++i) {
-            const int j = ids[i];
-            const int layers = hj[i].radius + 1;
-            int st_rc = status_to_rc(hj[i].status);
-            if (layers > cap) { st_rc = CG_EINVAL; rc = CG_EINVAL; }
-            nl_out[j] = layers;
-            for (int r = 0; r < layers && r < cap; ++r) layer_out[(uint64_t)j * cap + r] = lay[(uint64_t)i * lcap + r];
-            if (status_out) status_out[j] = st_rc;
-            if (st_rc < 0 && rc == CG_OK) rc = st_rc;
+        e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, b->grid, lcap + 1, kTimeoutNs, b->ilp, st);
+    const uint64_t o1 = al256(nj * sizeof(JobDev)), o2 = o1 + al256(sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_jobs, nj * sizeof(JobDev), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout + o1, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hout + o2, base + w.o_lay, (uint64_t)nj * lcap * 8, cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
+// Read one wave's results from host memory into the caller's arrays.
+int collect_wave(cg_batch* b, const cg_batch::Wave& w, const char* hres, int lcap, int cap,
+                 uint64_t* layer_out, int* nl_out, int* status_out) {
+    const int nj = (int)w.ids.size();
+    const JobDev* hj = reinterpret_cast<const JobDev*>(hres);
+    const uint64_t o1 = al256(nj * sizeof(JobDev)), o2 = o1 + al256(sizeof(Ctl));
+    const Ctl* ctl = reinterpret_cast<const Ctl*>(hres + o1);
+    const uint64_t* lay = reinterpret_cast<const uint64_t*>(hres + o2);
+    b->stats.rounds += ctl->rounds;
+    if (ctl->err) return ctl->err;
+    int rc = CG_OK;
+    for (int i = 0; i < nj; ++i) {
+        const int j = w.ids[i];
+        const int layers = hj[i].radius + 1;
+        int st_rc = status_to_rc(hj[i].status);
+        if (layers > cap) { st_rc = CG_EINVAL; rc = CG_EINVAL; }
+        nl_out[j] = layers;
+        for (int r = 0; r < layers && r < cap; ++r) layer_out[(uint64_t)j * cap + r] = lay[(uint64_t)i * lcap + r];
+        if (status_out) status_out[j] = st_rc;
+        if (st_rc < 0 && rc == CG_OK) rc = st_rc;
+    }
+    return rc;
+}
+
+// Choose visited sets, kernel variant, grid and waves; allocate the waves' buffers when they
+// fit together.
+int plan_batch(cg_batch* b, int dev, int cap, cudaStream_t st) {
+    b->release();
+    int maxk = 1;
+    bool any_bitmap = false;
+    for (auto& J : b->jobs) {
+        maxk = std::max(maxk, J.k);
+        const bool can_bitmap = J.k > 0 && J.n <= 12 && bitmap_fits(J.n, b->mem_cap);
+        J.mode = (b->visited == CG_STRATEGY_HASH) ? cg::kVisitHash
+                 : (b->visited == CG_STRATEGY_BITMAP) ? (can_bitmap ? cg::kVisitBitmap : cg::kVisitHash)
+                 : (can_bitmap && bitmap_eligible(J.n, J.order, b->mem_cap)) ? cg::kVisitBitmap
+                                                                              : cg::kVisitHash;
+        any_bitmap |= J.mode == cg::kVisitBitmap;
+    }
+    // The rank-bitmap kernel variant also runs hash-table jobs of the same launch.
+    const int base_ilp = b->ilp_override > 0 ? b->ilp_override : default_ilp(maxk, any_bitmap);
+    b->ilp = base_ilp + (any_bitmap ? 16 : 0);
+    b->stats.strategy_used = any_bitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
+    b->stats.probe_variant = b->ilp;
+    const int grid_max = grow_grid(dev, b->ilp, true);
+    if (grid_max <= 0) return CG_ECUDA;
+    b->grid = b->grid_override > 0 ? std::min(grid_max, b->grid_override) : grid_max;
+    const uint64_t budget = b->mem_cap;
+    const uint64_t per_job_max = max_cap_for_mem(budget / 2);
+    uint64_t l2_cap = b->wave_l2;
+    if (l2_cap == 0) {
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) {
+            cudaGetLastError();
+            l2 = 64 << 20;
+        }
+        l2_cap = (uint64_t)l2 / 2;
+    }
+    // Greedy waves in job order, each within the memory budget and with visited sets that
+    // together fit the L2 cap (a set larger than the cap misses L2 wherever it runs and does not
+    // count).  Jobs with no work (no generator, radius 0) are answered on the host.
+    const int lcap = cap + 1;
+    cg_batch::Wave cur;
+    uint64_t wave_bytes = 0, wave_vis = 0, total_bytes = 0;
+    auto close_wave = [&]() {
+        if (cur.ids.empty()) return;
+        layout_wave(b, cur, lcap);
+        total_bytes += cur.bytes;
+        b->waves.push_back(std::move(cur));
+        cur = cg_batch::Wave();
+        wave_bytes = wave_vis = 0;
+    };
+    for (int j = 0; j < (int)b->jobs.size(); ++j) {
+        auto& J = b->jobs[j];
+        if (J.k == 0 || J.max_radius == 0) continue;
+        J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
+        const uint64_t set_bytes = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) * 4
+                                                               : table_slots_for(J.cap) * 8;
+        const uint64_t need = J.cap * 8 + set_bytes + sizeof(GenSM) * J.gsm.size() +
+                              sizeof(JobDev) + (uint64_t)lcap * 8 + 1024;
+        const uint64_t vis = set_bytes <= l2_cap ? set_bytes : 0;
+        if (!cur.ids.empty() && (wave_bytes + need > budget || wave_vis + vis > l2_cap)) close_wave();
+        cur.ids.push_back(j);
+        wave_bytes += need;
+        wave_vis += vis;
+    }
+    close_wave();
+    // pinned host memory for every wave's results
+    uint64_t hb = 0;
+    for (auto& w : b->waves) {
+        w.h_off = hb;
+        hb += al256(wave_result_bytes(w, lcap));
+    }
+    if (hb) {
+        if (cudaMallocHost(reinterpret_cast<void**>(&b->h_pinned), hb) != cudaSuccess) {
+            cudaGetLastError();
+            return CG_ENOMEM;
+        }
+        b->h_bytes = hb;
+    }
+    // resident when all waves fit the budget together
+    b->resident = total_bytes <= budget;
+    if (b->resident) {
+        for (auto& w : b->waves) {
+            w.base = (char*)dev_alloc(w.bytes, st);
+            if (!w.base) { b->release(); return CG_ENOMEM; }
+            cudaError_t e = bind_wave(w, w.base, st);
+            if (e != cudaSuccess) { b->release(); return cuda_rc(e); }
+            b->stats.h2d_bytes += w.hg.size() * sizeof(GenSM) + w.hj.size() * sizeof(JobDev);
         }
     }
-    dev_free(base, st);
-    cudaStreamSynchronize(st);
-    return rc;
+    b->planned = true;
+    b->plan_cap = cap;
+    b->device = dev;
+    return CG_OK;
+}
+
+// Enqueue a whole run of a resident plan (every wave).
+cudaError_t enqueue_resident_run(cg_batch* b, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    const int lcap = b->plan_cap + 1;
+    for (auto& w : b->waves) {
+        if (e != cudaSuccess) break;
+        e = enqueue_wave(b, w, w.base, b->h_pinned + w.h_off, lcap, st);
+    }
+    return e;
 }
 
 }  // namespace
@@ -1253,71 +1453,127 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_rc(e);
-    int maxk = 1;
-    bool any_bitmap = false;
-    for (auto& J : b->jobs) {
-        maxk = std::max(maxk, J.k);
-        J.mode = (J.k > 0 && J.n <= 12 && bitmap_eligible(J.n, J.order, b->mem_cap)) ? cg::kVisitBitmap
-                                                                                     : cg::kVisitHash;
-        any_bitmap |= J.mode == cg::kVisitBitmap;
-    }
-    // The rank-bitmap kernel variant also runs hash-table jobs of the same launch.
-    const int ilp = default_ilp(maxk, any_bitmap) + (any_bitmap ? 16 : 0);
-    b->stats.strategy_used = any_bitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
-    b->stats.probe_variant = ilp;
-    const int grid = grow_grid(dev, ilp, true);
-    if (grid <= 0) return CG_ECUDA;
-    const uint64_t budget = b->mem_cap;
-    const uint64_t per_job_max = max_cap_for_mem(budget / 2);
-    uint64_t l2_cap = b->wave_l2;
-    if (l2_cap == 0) {
-        int l2 = 0;
-        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) {
-            cudaGetLastError();
-            l2 = 64 << 20;
-        }
-        l2_cap = (uint64_t)l2 / 2;
-    }
-    // Greedy waves in job order, each within the memory budget and with visited sets that
-    // together fit the L2 cap (a set larger than the cap misses L2 wherever it runs and does not
-    // count).
-    std::vector<int> wave;
-    uint64_t wave_bytes = 0, wave_vis = 0;
-    int rc = CG_OK;
-    auto flush = [&]() {
-        int r = run_wave(b, wave, st, layer_sizes_out, cap, num_layers_out, status_out, grid, ilp);
-        if (r != CG_OK && rc == CG_OK) rc = r;
-        wave.clear();
-        wave_bytes = 0;
-        wave_vis = 0;
-    };
+    if (!b->ev0 && (e = cudaEventCreate(&b->ev0)) != cudaSuccess) return cuda_rc(e);
+    if (!b->ev1 && (e = cudaEventCreate(&b->ev1)) != cudaSuccess) return cuda_rc(e);
+    // jobs with no work
     for (int j = 0; j < (int)b->jobs.size(); ++j) {
-        auto& J = b->jobs[j];
+        const auto& J = b->jobs[j];
         if (J.k == 0 || J.max_radius == 0) {
             num_layers_out[j] = 1;
             layer_sizes_out[(uint64_t)j * cap] = 1;
             if (status_out) status_out[j] = J.k == 0 ? CG_OK : CG_TRUNC_RADIUS;
-            continue;
         }
-        J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
-        const uint64_t set_bytes = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) * 4
-                                                               : table_slots_for(J.cap) * 8;
-        const uint64_t need = J.cap * 8 + set_bytes + sizeof(GenSM) * J.gsm.size() +
-                              sizeof(JobDev) + (uint64_t)(cap + 1) * 8 + 1024;
-        const uint64_t vis = set_bytes <= l2_cap ? set_bytes : 0;
-        if (!wave.empty() && (wave_bytes + need > budget || wave_vis + vis > l2_cap)) flush();
-        wave.push_back(j);
-        wave_bytes += need;
-        wave_vis += vis;
     }
-    if (!wave.empty()) flush();
+    int rc = CG_OK;
+    if (!b->planned || b->plan_cap != cap || b->device != dev) {
+        if ((rc = plan_batch(b, dev, cap, st)) != CG_OK) return rc;
+    } else {
+        b->stats.strategy_used = b->ilp >= 16 ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
+        b->stats.probe_variant = b->ilp;
+    }
+    const int lcap = cap + 1;
+    if (b->resident) {
+        if (b->use_graph > 0 && !b->gexec) {
+            // capture the run once (a legacy-default stream cannot be captured: use our own)
+            if (!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                b->use_graph = -1;
+            }
+            if (b->use_graph > 0) {
+                cudaStreamSynchronize(st);
+                e = cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t ee = enqueue_resident_run(b, b->gstream);
+                    e = cudaStreamEndCapture(b->gstream, &b->graph);
+                    if (ee != cudaSuccess) e = ee;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+                if (e != cudaSuccess) {         // capture not possible here: run without a graph
+                    cudaGetLastError();
+                    b->drop_graph();
+                    b->use_graph = -1;
+                }
+            }
+        }
+        if (b->gexec) {
+            // the replay starts after the caller's stream's earlier work (ev0 recorded there)
+            if ((e = cudaEventRecord(b->ev0, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaStreamWaitEvent(b->gstream, b->ev0, 0)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaGraphLaunch(b->gexec, b->gstream)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaEventRecord(b->ev1, b->gstream)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaStreamSynchronize(b->gstream)) != cudaSuccess) return cuda_rc(e);
+            b->stats.launches += 1;     // one graph: its kernels are counted below
+        } else {
+            if ((e = cudaEventRecord(b->ev0, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = enqueue_resident_run(b, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaEventRecord(b->ev1, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        }
+        b->stats.kernel_ms += elapsed_ms(b->ev0, b->ev1);
+        for (auto& w : b->waves) {
+            b->stats.launches += 3;     // init_jobs + init_units + grow
+            b->stats.d2h_bytes += wave_result_bytes(w, lcap);
+            int r = collect_wave(b, w, b->h_pinned + w.h_off, lcap, cap, layer_sizes_out,
+                                 num_layers_out, status_out);
+            if (r != CG_OK && rc == CG_OK) rc = r;
+        }
+        return rc;
+    }
+    // Not resident: each wave's buffer is allocated, run and freed in turn.
+    for (auto& w : b->waves) {
+        char* base = (char*)dev_alloc(w.bytes, st);
+        if (!base) return CG_ENOMEM;
+        e = bind_wave(w, base, st);
+        b->stats.h2d_bytes += w.hg.size() * sizeof(GenSM) + w.hj.size() * sizeof(JobDev);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev0, st);
+        if (e == cudaSuccess) e = enqueue_wave(b, w, base, b->h_pinned + w.h_off, lcap, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev1, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) b->stats.kernel_ms += elapsed_ms(b->ev0, b->ev1);
+        dev_free(base, st);
+        cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_rc(e);
+        b->stats.launches += 3;
+        b->stats.d2h_bytes += wave_result_bytes(w, lcap);
+        int r = collect_wave(b, w, b->h_pinned + w.h_off, lcap, cap, layer_sizes_out, num_layers_out,
+                             status_out);
+        if (r != CG_OK && rc == CG_OK) rc = r;
+    }
     return rc;
 }
 
-int cg_batch_set_wave_l2(cg_batch_t b, uint64_t bytes) {
+int cg_batch_set_option(cg_batch_t b, int option, int64_t value) {
     if (!b) return CG_EINVAL;
-    b->wave_l2 = bytes;
+    switch (option) {
+        case CG_OPT_ILP:
+            if (value < 0 || value > 4) return CG_EINVAL;
+            b->ilp_override = (int)value;
+            break;
+        case CG_OPT_GRID:
+            if (value < 0 || value > (1 << 20)) return CG_EINVAL;
+            b->grid_override = (int)value;
+            break;
+        case CG_OPT_BATCH_WAVE_L2:
+            b->wave_l2 = value < 0 ? ~0ull : (uint64_t)value;
+            break;
+        case CG_OPT_BATCH_VISITED:
+            if (value != CG_STRATEGY_AUTO && value != CG_STRATEGY_HASH && value != CG_STRATEGY_BITMAP)
+                return CG_EINVAL;
+            b->visited = (int)value;
+            break;
+        case CG_OPT_GRAPH:
+            b->use_graph = value ? 1 : 0;
+            b->drop_graph();
+            return CG_OK;
+        default:
+            return CG_EINVAL;
+    }
+    if (b->planned) b->release();
     return CG_OK;
+}
+
+int cg_batch_set_wave_l2(cg_batch_t b, uint64_t bytes) {
+    return cg_batch_set_option(b, CG_OPT_BATCH_WAVE_L2, bytes == ~0ull ? -1 : (int64_t)bytes);
 }
 
 int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out) {
@@ -1327,8 +1583,11 @@ int cg_batch_get_stats(cg_batch_t b, cg_growth_stats* out) {
 }
 
 int cg_batch_destroy(cg_batch_t b) {
-    if (b && b->ev0) cudaEventDestroy(b->ev0);
-    if (b && b->ev1) cudaEventDestroy(b->ev1);
+    if (!b) return CG_OK;
+    b->release();
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
     return CG_OK;
 }

@@ -333,6 +333,7 @@ SortScratch carve_sort_scratch(void* scratch, unsigned long long n) {
 
 cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,
                               uint64_t* out, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (F == 0) return cudaSuccess;
     unsigned long long blocks = (F + kBlock - 1) / kBlock;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
@@ -344,6 +345,7 @@ cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, un
 // number of 8-bit passes is ceil(bits / 8), an odd count ends with one extra copy.
 cudaError_t launch_radix_sort(uint64_t* keys, unsigned long long n, int bits, const SortScratch& s,
                               cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (n <= 1) return cudaSuccess;
     const int nt = tiles_of(n);
     const unsigned long long hist_n = (unsigned long long)kDigits * nt;
@@ -372,6 +374,7 @@ cudaError_t launch_radix_sort(uint64_t* keys, unsigned long long n, int bits, co
 cudaError_t launch_unique_difference(const uint64_t* a, unsigned long long na, const uint64_t* const* bs,
                                      const unsigned long long* nbs, int nb_sets, uint64_t* out,
                                      unsigned long long* d_count, const SortScratch& s, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (na == 0) return cudaMemsetAsync(d_count, 0, 8, st);
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < (nb_sets > 0 ? nb_sets : 1) && e == cudaSuccess; ++j) {

@@ -423,6 +423,7 @@ __global__ void pos_unrank_kernel(const uint64_t* ranks, unsigned long long coun
 template <template <int> class K, int... Ns, typename... A>
 cudaError_t launch_by_n_impl(std::integer_sequence<int, Ns...>, int n, int grid, cudaStream_t st,
                              A... args) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     cudaError_t e = cudaErrorInvalidValue;
     (void)((n == Ns + 1 ? (K<Ns + 1>::launch(grid, st, args...), e = cudaGetLastError(), 0) : 0) + ...);
     return e;
@@ -430,6 +431,7 @@ cudaError_t launch_by_n_impl(std::integer_sequence<int, Ns...>, int n, int grid,
 
 template <template <int> class K, typename... A>
 cudaError_t launch_by_n(int n, int grid, cudaStream_t st, A... args) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     return launch_by_n_impl<K>(std::make_integer_sequence<int, 16>{}, n, grid, st, args...);
 }
 
@@ -464,12 +466,14 @@ int sweep_max_grid(int device, int ilp, int n) {
 }
 
 cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     sweep_init_kernel<<<1, 32, 0, st>>>(d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
                               int ilp, int n, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     const sweep_fn_t f = sweep_fn(ilp, n);
     if (!f) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
@@ -488,18 +492,21 @@ cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, u
 cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,
                                 uint64_t* out, unsigned long long cap, unsigned long long* count,
                                 int grid, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (nlist == 0) return cudaSuccess;
     return launch_by_n<ExportK>(n, grid, st, F, L, nlist, out, cap, count);
 }
 
 cudaError_t launch_pos_rank(const uint64_t* keys, unsigned long long count, int n, uint64_t* out,
                             int grid, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (count == 0) return cudaSuccess;
     return launch_by_n<RankK>(n, grid, st, keys, count, out);
 }
 
 cudaError_t launch_pos_unrank(const uint64_t* ranks, unsigned long long count, int n, uint64_t* out,
                               int grid, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (count == 0) return cudaSuccess;
     return launch_by_n<UnrankK>(n, grid, st, ranks, count, out);
 }
