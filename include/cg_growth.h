@@ -121,7 +121,9 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
  * Grow from a central state instead of the identity (Section 3.1.2: a Schreier coset graph is
  * given by a vector whose stabiliser is the subgroup; its growth is that of the vector's orbit,
  * Section 5.2).  start: host pointer, n values in 0..15, repeats allowed; copied.  NULL restores
- * the identity.  A start with repeated values needs the HASH or SORT strategy (AUTO picks HASH;
+ * the identity.  States are packed with the narrowest element width w of 1, 2, 4 bits that
+ * holds the values (4 for a permutation), so n * w <= 64: binary vectors up to n = 64 (the
+ * handle is created with n up to 64; a growth from the identity needs n <= 16).  A start with repeated values needs the HASH or SORT strategy (AUTO picks HASH;
  * BITMAP then fails at run with CG_EINVAL).  Releases buffers sized for an earlier start.
  * Errors: CG_EINVAL.
  */
@@ -144,9 +146,16 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
                   int* num_layers_out);
 
 /*
+ * Bits per element of the packed keys of a growth: 4 for permutations, and for a start vector
+ * with repeated values the narrowest of 1, 2, 4 that holds its largest value (element i in bits
+ * [w i, w i + w)).  Returns 0 for a NULL handle.
+ */
+int cg_growth_key_width(cg_growth_t h);
+
+/*
  * Copy the packed keys of the last reported layer (the antipodes when the growth ended) to
- * host memory keys_out (room for cap keys), in no particular order; *count_out receives the
- * layer size.  Needs CG_OPT_KEEP_LAST = 1 before the run.  Errors: CG_EINVAL (cap too small:
+ * host memory keys_out (room for cap keys), in no particular order, element i of a state in
+ * bits [w i, w i + w) with w = cg_growth_key_width(h); *count_out receives the layer size.  Needs CG_OPT_KEEP_LAST = 1 before the run.  Errors: CG_EINVAL (cap too small:
  * *count_out still written), CG_ECUDA.
  */
 int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64_t* count_out);

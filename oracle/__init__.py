@@ -39,6 +39,9 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_PROGRESS = ctypes.CFUNCTYPE(None, ctypes.c_int, ctypes.c_uint64)
+
+
 def _load():
     global _lib
     with _lock:
@@ -63,6 +66,10 @@ def _load():
                                                  ctypes.c_uint64, ctypes.c_int, u64p, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int)]
             lib.oracle_growth_bitmap.restype = ctypes.c_int
+            lib.oracle_growth_bitmask.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int,
+                                                  ctypes.c_uint64, ctypes.c_int, u64p, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int), _PROGRESS]
+            lib.oracle_growth_bitmask.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -111,6 +118,25 @@ def growth_bitmap(n: int, gens: Sequence[Sequence[int]], max_radius: int = -1,
                                   ctypes.byref(nl))
     if rc < 0:
         raise ValueError(f"oracle_growth_bitmap failed rc={rc}")
+    return [int(x) for x in out[:nl.value]], rc
+
+
+def growth_bitmask(n: int, gens: Sequence[Sequence[int]], max_radius: int = -1,
+                   stop_above: int = 0, threads: int = 0, progress=None) -> Tuple[List[int], int]:
+    """Oracle C: the same growth with the visited set and the current and next layers as bitmaps
+    over all n! permutations (n <= 14; 3 n!/8 bytes of host memory).  progress(radius, size) is
+    called after each layer when given."""
+    lib = _load()
+    g = _gens_array(n, gens)
+    cap = 4096
+    out = np.zeros(cap, dtype=np.uint64)
+    nl = ctypes.c_int(0)
+    cb = _PROGRESS(progress) if progress else _PROGRESS()
+    rc = lib.oracle_growth_bitmask(n, len(gens), _ptr(g, ctypes.c_uint8), int(max_radius),
+                                   int(stop_above), int(threads), _ptr(out, ctypes.c_uint64), cap,
+                                   ctypes.byref(nl), cb)
+    if rc < 0:
+        raise ValueError(f"oracle_growth_bitmask failed rc={rc}")
     return [int(x) for x in out[:nl.value]], rc
 
 

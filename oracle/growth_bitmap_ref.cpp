@@ -10,6 +10,15 @@
  * is a list of permutations (one byte per element); the expansion is split over threads, each
  * claiming bits with an atomic fetch-or.  Checked against oracle A in tests/test_oracle_pins.py.
  *
+ * ORACLE C (oracle_growth_bitmask, same file): the same BFS with the frontier too kept as a
+ * bitmap over the n! ranks (the paper's bitmask BFS of Section 3.1.3: bits per element of the
+ * group instead of a list of states), so that the whole of S_14 (87,178,291,200 states) fits in
+ * host memory: three bitmaps of n!/8 bytes (seen, current layer, next layer), 32.7 GB for n = 14.
+ * Each layer step visits the set bits of the current layer in rank order, unranks each (the
+ * factorial-base digits, each picking the c-th smallest unused value), applies every generator,
+ * ranks the image and claims its bit in `seen`; a new state also sets its bit in the next layer.
+ * Pinned to oracle A and oracle B in tests/test_oracle_pins.py.
+ *
  * Only tests/ and the committed golden-value script may call this code.
  */
 #include <algorithm>
@@ -48,6 +57,39 @@ uint64_t lehmer_rank(const uint8_t* p, int n, const uint64_t* fact) {
         for (int j = i + 1; j < n; ++j)
             if (p[j] < p[i]) ++c;
         r += c * fact[n - 1 - i];
+    }
+    return r;
+}
+
+// Inverse of lehmer_rank: digit c_i = (r / (n-1-i)!) mod (n-i); position i takes the c_i-th
+// smallest of the values not yet used.
+void lehmer_unrank(uint64_t r, int n, const uint64_t* fact, uint8_t* p) {
+    unsigned unused = (1u << n) - 1u;
+    for (int i = 0; i < n; ++i) {
+        const uint64_t w = fact[n - 1 - i];
+        unsigned c = (unsigned)(r / w);
+        r -= (uint64_t)c * w;
+        int v = 0;
+        for (;; ++v) {
+            if ((unused >> v) & 1u) {
+                if (c == 0) break;
+                --c;
+            }
+        }
+        p[i] = (uint8_t)v;
+        unused &= ~(1u << v);
+    }
+}
+
+// lehmer_rank with the count of smaller elements to the right taken from a bit mask of the
+// values at positions > i (the same definition, c_i = #{ j > i : p[j] < p[i] }).
+uint64_t lehmer_rank_mask(const uint8_t* p, int n, const uint64_t* fact) {
+    uint64_t r = 0;
+    unsigned right = 0;
+    for (int i = n - 1; i >= 0; --i) {
+        const unsigned c = (unsigned)__builtin_popcount(right & ((1u << p[i]) - 1u));
+        right |= 1u << p[i];
+        r += (uint64_t)c * fact[n - 1 - i];
     }
     return r;
 }
@@ -139,6 +181,103 @@ int oracle_growth_bitmap(int n, int k, const uint8_t* gens, int max_radius, uint
         frontier.swap(next);
         layers.push_back(count);
         ++radius;
+    }
+    *num_layers = (int)layers.size();
+    for (int r = 0; r < (int)layers.size() && r < cap; ++r) out[r] = layers[r];
+    if ((int)layers.size() > cap) return -2;
+    return rc;
+}
+
+/*
+ * Oracle C: growth from the identity with the visited set and the current and next layers as
+ * bitmaps over the n! Lehmer ranks.  Arguments and return codes as oracle_growth_bitmap.
+ * progress, when not NULL, is called after each layer with its radius and size.
+ */
+int oracle_growth_bitmask(int n, int k, const uint8_t* gens, int max_radius, uint64_t stop_above,
+                          int threads, uint64_t* out, int cap, int* num_layers,
+                          void (*progress)(int, uint64_t)) {
+    if (!valid(n, k, gens) || !num_layers || n > 14) return -1;
+    uint64_t fact[17];
+    for (int i = 0; i <= 16; ++i) fact[i] = factorial(i);
+    const uint64_t total = fact[n];
+    const uint64_t words = (total + 63) / 64;
+    std::vector<std::atomic<uint64_t>> seen, cur, nxt;
+    try {
+        seen = std::vector<std::atomic<uint64_t>>(words);
+        cur = std::vector<std::atomic<uint64_t>>(words);
+        nxt = std::vector<std::atomic<uint64_t>>(words);
+    } catch (...) {
+        return -3;
+    }
+    if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    auto parallel = [&](auto&& body) {   // body(word_begin, word_end) over chunks of the words
+        std::atomic<uint64_t> next_chunk{0};
+        const uint64_t chunk = 1u << 14;
+        std::vector<std::thread> pool;
+        for (int t = 0; t < threads; ++t)
+            pool.emplace_back([&]() {
+                for (;;) {
+                    const uint64_t c = next_chunk.fetch_add(1);
+                    const uint64_t b = c * chunk;
+                    if (b >= words) break;
+                    body(b, std::min(words, b + chunk));
+                }
+            });
+        for (auto& th : pool) th.join();
+    };
+    parallel([&](uint64_t b, uint64_t e) {
+        for (uint64_t w = b; w < e; ++w) {
+            seen[w].store(0, std::memory_order_relaxed);
+            cur[w].store(0, std::memory_order_relaxed);
+            nxt[w].store(0, std::memory_order_relaxed);
+        }
+    });
+    {
+        std::vector<uint8_t> id(n);
+        for (int i = 0; i < n; ++i) id[i] = (uint8_t)i;
+        const uint64_t r0 = lehmer_rank_mask(id.data(), n, fact);
+        seen[r0 / 64].fetch_or(1ull << (r0 % 64));
+        cur[r0 / 64].fetch_or(1ull << (r0 % 64));
+    }
+    std::vector<uint64_t> layers{1};
+    int rc = 0;
+    int radius = 0;
+    for (;;) {
+        if (max_radius >= 0 && radius >= max_radius) { rc = 1; break; }
+        if (stop_above > 0 && layers.back() > stop_above) { rc = 1; break; }
+        std::atomic<uint64_t> count{0};
+        parallel([&](uint64_t b, uint64_t e) {
+            std::vector<uint8_t> s(n), t(n);
+            uint64_t mine = 0;
+            for (uint64_t w = b; w < e; ++w) {
+                uint64_t bits = cur[w].load(std::memory_order_relaxed);
+                while (bits) {
+                    const int bit = __builtin_ctzll(bits);
+                    bits &= bits - 1;
+                    lehmer_unrank(w * 64 + (uint64_t)bit, n, fact, s.data());
+                    for (int j = 0; j < k; ++j) {
+                        for (int i = 0; i < n; ++i) t[i] = s[gens[j * n + i]];   // t[i] = s[g[i]]
+                        const uint64_t r = lehmer_rank_mask(t.data(), n, fact);
+                        const uint64_t m = 1ull << (r % 64);
+                        if (!(seen[r / 64].fetch_or(m, std::memory_order_relaxed) & m)) {
+                            nxt[r / 64].fetch_or(m, std::memory_order_relaxed);
+                            ++mine;
+                        }
+                    }
+                }
+            }
+            count.fetch_add(mine);
+        });
+        const uint64_t c = count.load();
+        if (c == 0) break;
+        layers.push_back(c);
+        ++radius;
+        if (progress) progress(radius, c);
+        // the next layer becomes the current one; the old current layer is cleared
+        cur.swap(nxt);
+        parallel([&](uint64_t b, uint64_t e) {
+            for (uint64_t w = b; w < e; ++w) nxt[w].store(0, std::memory_order_relaxed);
+        });
     }
     *num_layers = (int)layers.size();
     for (int r = 0; r < (int)layers.size() && r < cap; ++r) out[r] = layers[r];

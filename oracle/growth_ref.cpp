@@ -41,8 +41,38 @@ uint64_t key_of(const uint8_t* p, int n) {
     return key;
 }
 
-bool valid_gens(int n, int k, const uint8_t* gens) {
-    if (n < 1 || n > 16 || k < 1 || gens == nullptr) return false;
+// Injective key of a vector of up to 64 values below 16 (element i in bits [4i, 4i+4) of a
+// 256-bit number), for the orbits of long vectors (Schreier coset graphs with n > 16).
+struct WideKey {
+    uint64_t w[4];
+    bool operator==(const WideKey& o) const {
+        return w[0] == o.w[0] && w[1] == o.w[1] && w[2] == o.w[2] && w[3] == o.w[3];
+    }
+};
+struct WideHash {
+    size_t operator()(const WideKey& k) const {
+        return std::hash<uint64_t>()(k.w[0] ^ (k.w[1] * 0x9E3779B97F4A7C15ull) ^
+                                     (k.w[2] * 0xC2B2AE3D27D4EB4Full) ^ (k.w[3] * 0x165667B19E3779F9ull));
+    }
+};
+
+struct NarrowKeys {
+    using Key = uint64_t;
+    using Set = std::unordered_set<uint64_t>;
+    static Key of(const uint8_t* p, int n) { return key_of(p, n); }
+};
+struct WideKeys {
+    using Key = WideKey;
+    using Set = std::unordered_set<WideKey, WideHash>;
+    static Key of(const uint8_t* p, int n) {
+        WideKey k{{0, 0, 0, 0}};
+        for (int i = 0; i < n; ++i) k.w[i / 16] |= (uint64_t)p[i] << (4 * (i % 16));
+        return k;
+    }
+};
+
+bool valid_gens(int n, int k, const uint8_t* gens, int max_n = 16) {
+    if (n < 1 || n > max_n || k < 1 || gens == nullptr) return false;
     for (int j = 0; j < k; ++j) {
         std::vector<int> hit(n, 0);
         for (int i = 0; i < n; ++i) {
@@ -59,37 +89,39 @@ void apply(const uint8_t* s, const uint8_t* g, uint8_t* t, int n) {
     for (int i = 0; i < n; ++i) t[i] = s[g[i]];
 }
 
-struct Bfs {
+template <class Keys>
+struct BfsT {
+    using Key = typename Keys::Key;
     int n, k;
     const uint8_t* gens;
     bool two_layer;
-    std::unordered_set<uint64_t> seen;                 // full-visited mode
-    std::unordered_set<uint64_t> prev, cur;            // two-layer mode
+    typename Keys::Set seen;                           // full-visited mode
+    typename Keys::Set prev, cur;                      // two-layer mode
     std::vector<uint8_t> frontier;                     // n bytes per state
     uint64_t frontier_count = 0;
     int radius = 0;
 
     // Breadth-first search from `start` (n values, repeats allowed: the orbit of a vector under
     // the group, i.e. a Schreier coset graph, Sections 3.1.2 and 5.2), or from the identity.
-    Bfs(int n_, int k_, const uint8_t* g_, bool two, const uint8_t* start = nullptr)
+    BfsT(int n_, int k_, const uint8_t* g_, bool two, const uint8_t* start = nullptr)
         : n(n_), k(k_), gens(g_), two_layer(two) {
         frontier.resize(n);
         for (int i = 0; i < n; ++i) frontier[i] = start ? start[i] : (uint8_t)i;
         frontier_count = 1;
-        uint64_t id = key_of(frontier.data(), n);
+        const Key id = Keys::of(frontier.data(), n);
         if (two_layer) cur.insert(id); else seen.insert(id);
     }
 
     // One BFS step: returns the size of the next layer and makes it the frontier.
     uint64_t step() {
         std::vector<uint8_t> next;
-        std::unordered_set<uint64_t> next_set;
+        typename Keys::Set next_set;
         std::vector<uint8_t> t(n);
         for (uint64_t s = 0; s < frontier_count; ++s) {
             const uint8_t* st = &frontier[s * n];
             for (int j = 0; j < k; ++j) {
                 apply(st, gens + j * n, t.data(), n);
-                uint64_t key = key_of(t.data(), n);
+                const Key key = Keys::of(t.data(), n);
                 bool fresh;
                 if (two_layer) {
                     // Only valid for inverse-closed sets: every neighbour of layer r lies in
@@ -113,28 +145,10 @@ struct Bfs {
     }
 };
 
-}  // namespace
+using Bfs = BfsT<NarrowKeys>;
 
-extern "C" {
-
-/*
- * Growth vector of <gens> from the identity (oracle_growth) or from the vector `start`
- * (oracle_growth_from; n values in 0..15, repeats allowed).
- *   two_layer   0: full visited set (any generating set); 1: keep only layers r-1 and r
- *               (correct only for inverse-closed sets; the tests check it against mode 0).
- *   max_radius  < 0: unlimited; else stop after layer max_radius.
- *   stop_above  > 0: stop after the first layer whose size exceeds this value.
- * Writes gamma(0..R) to out[0..cap) and R+1 to *num_layers.
- * Returns 0 when the growth ended (empty next layer), 1 when stopped by max_radius or
- * stop_above, -1 on invalid input, -2 when cap was too small (*num_layers still exact).
- */
-int oracle_growth_from(int n, int k, const uint8_t* gens, const uint8_t* start, int two_layer,
-                       int max_radius, uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
-    if (!valid_gens(n, k, gens) || num_layers == nullptr) return -1;
-    if (start)
-        for (int i = 0; i < n; ++i)
-            if (start[i] > 15) return -1;
-    Bfs bfs(n, k, gens, two_layer != 0, start);
+template <class B>
+int run_growth(B& bfs, int max_radius, uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
     std::vector<uint64_t> layers{1};
     int rc = 0;
     while (true) {
@@ -148,6 +162,36 @@ int oracle_growth_from(int n, int k, const uint8_t* gens, const uint8_t* start, 
     for (int r = 0; r < (int)layers.size() && r < cap; ++r) out[r] = layers[r];
     if ((int)layers.size() > cap) return -2;
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+/*
+ * Growth vector of <gens> from the identity (oracle_growth, n <= 16) or from the vector `start`
+ * (oracle_growth_from; n <= 64 values in 0..15, repeats allowed).
+ *   two_layer   0: full visited set (any generating set); 1: keep only layers r-1 and r
+ *               (correct only for inverse-closed sets; the tests check it against mode 0).
+ *   max_radius  < 0: unlimited; else stop after layer max_radius.
+ *   stop_above  > 0: stop after the first layer whose size exceeds this value.
+ * Writes gamma(0..R) to out[0..cap) and R+1 to *num_layers.
+ * Returns 0 when the growth ended (empty next layer), 1 when stopped by max_radius or
+ * stop_above, -1 on invalid input, -2 when cap was too small (*num_layers still exact).
+ */
+int oracle_growth_from(int n, int k, const uint8_t* gens, const uint8_t* start, int two_layer,
+                       int max_radius, uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
+    // n up to 64 when a start vector is given (values below 16), up to 16 from the identity
+    if (!valid_gens(n, k, gens, start ? 64 : 16) || num_layers == nullptr) return -1;
+    if (start)
+        for (int i = 0; i < n; ++i)
+            if (start[i] > 15) return -1;
+    if (n <= 16) {
+        BfsT<NarrowKeys> bfs(n, k, gens, two_layer != 0, start);
+        return run_growth(bfs, max_radius, stop_above, out, cap, num_layers);
+    }
+    BfsT<WideKeys> bfs(n, k, gens, two_layer != 0, start);
+    return run_growth(bfs, max_radius, stop_above, out, cap, num_layers);
 }
 
 int oracle_growth(int n, int k, const uint8_t* gens, int two_layer, int max_radius,

@@ -67,6 +67,7 @@ SIGNATURES = {
     "cg_growth_destroy": (ctypes.c_int, [_vp]),
     "cg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "cg_last_error_detail": (ctypes.c_char_p, []),
+    "cg_growth_key_width": (ctypes.c_int, [_vp]),
     "cg_batch_create": (ctypes.c_int, [ctypes.c_int, _ip, _ip, _u8p, _u64p, _ip, _ip, ctypes.c_uint64,
                                        ctypes.POINTER(_vp)]),
     "cg_batch_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip, _ip]),
@@ -145,6 +146,7 @@ cg_growth_get_stats = _export("cg_growth_get_stats")
 cg_growth_destroy = _export("cg_growth_destroy")
 cg_strerror = _export("cg_strerror")
 cg_last_error_detail = _export("cg_last_error_detail")
+cg_growth_key_width = _export("cg_growth_key_width")
 cg_batch_create = _export("cg_batch_create")
 cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")

@@ -180,6 +180,18 @@ class Growth:
                                            cnt.value, ctypes.byref(cnt)), "cg_growth_last_layer")
         return out[:cnt.value]
 
+    @property
+    def key_width(self) -> int:
+        """Bits per element of the packed keys (4 for permutations; 1 or 2 for narrow vectors)."""
+        return int(_cg.cg_growth_key_width(self._h))
+
+    def last_layer_vectors(self) -> np.ndarray:
+        """The last layer as an array of shape (count, n): the unpacked states."""
+        keys = self.last_layer()
+        w = self.key_width
+        shifts = (w * np.arange(self.n, dtype=np.uint64)).astype(np.uint64)
+        return ((keys[:, None] >> shifts[None, :]) & np.uint64((1 << w) - 1)).astype(np.uint8)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _cg.cg_growth_destroy(self._h)

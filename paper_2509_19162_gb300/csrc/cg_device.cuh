@@ -14,8 +14,19 @@ __device__ __forceinline__ uint64_t rotl64(uint64_t x, unsigned r) {
     return (x << r) | (x >> ((64u - r) & 63u));
 }
 
-// t[i] = s[g[i]] on 4-bit packed keys, as a union of rotated, masked copies of s.
+// t[i] = s[g[i]] on packed keys (see GenSM): a range reversal by bit reversal, otherwise a union
+// of rotated, masked copies of s.  kRev = false compiles the shift-and-mask form only: for
+// kernels that run generators of at most 16 elements, where reversals are in that form.
+template <bool kRev = true>
 __device__ __forceinline__ uint64_t apply_gen(const GenSM& g, uint64_t s) {
+    if (kRev && g.kind == 1) {
+        uint64_t r = __brevll(s);
+        if (g.width >= 2) r = ((r >> 1) & 0x5555555555555555ull) | ((r & 0x5555555555555555ull) << 1);
+        if (g.width == 4) r = ((r >> 2) & 0x3333333333333333ull) | ((r & 0x3333333333333333ull) << 2);
+        const int sh = g.rev_shift;
+        r = sh >= 0 ? (r >> sh) : (r << -sh);
+        return (s & ~g.mask[0]) | (r & g.mask[0]);
+    }
     uint64_t t = 0;
     const uint32_t nt = g.nterms;
 #pragma unroll 4

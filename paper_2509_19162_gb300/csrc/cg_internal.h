@@ -7,23 +7,35 @@
 namespace cg {
 
 constexpr uint64_t kEmpty = ~0ull;   // empty hash slot: never a valid permutation key, n >= 2
-constexpr int kMaxN = 16;
+constexpr int kMaxN = 16;            // permutations from the identity: 4 bits per element
+constexpr int kMaxElems = 64;        // coset vectors: n elements of `width` bits, n * width <= 64
+constexpr int kMaxTerms = 16;
 constexpr int kMaxLayers = 16384;    // device layer-size array per job
 
-// A generator in shift-and-mask form.  The gather t[i] = s[g[i]] moves nibble g[i] to nibble
-// i, a rotation of the packed key by 4*(i - g[i]) bits.  Positions sharing one offset form one
-// term: t = OR_t rotl(s, rot[t]) & mask[t].  Cyclic shifts need 2 terms, adjacent
-// transpositions 3, a prefix reversal of length j needs j+1 at most, any generator <= n.
+// A generator acting on packed keys (element i in bits [w i, w i + w), w = 1, 2 or 4).
+// kind 0, shift-and-mask form: the gather t[i] = s[g[i]] moves element g[i] to element i, a
+// rotation of the key by w*(i - g[i]) bits; positions sharing one offset form one term:
+// t = OR_t rotl(s, rot[t]) & mask[t].  Cyclic shifts need 2 terms, adjacent transpositions 3,
+// any generator <= n, so every generator of n <= 16 elements.
+// kind 1, the reversal of the element range [a, b], for long vectors where it would need more
+// than kMaxTerms terms: the whole key is bit-reversed (elements land in reverse order, each
+// with its bits reversed), the bits of every element put back in order, and the result shifted
+// so that element e lands on a + b - e: t = (s & ~mask[0]) | (shift(rev(s), rev_shift) & mask[0]).
+// Other generators of more than kMaxTerms offsets are not supported (CG_EINVAL at create).
 struct GenSM {
     uint32_t nterms;
     uint32_t inv_tag;   // 1 + index of this generator's inverse in the set (< 15), or 0
-    uint8_t rot[kMaxN];
-    uint64_t mask[kMaxN];
+    uint8_t kind;
+    uint8_t width;      // bits per element
+    int16_t rev_shift;  // kind 1: right shift (bits) of the reversed key; negative: left shift
+    uint8_t rot[kMaxTerms];
+    uint64_t mask[kMaxTerms];
 };
 
 // States found by generator j are stored with tag (1 + index of j's inverse) in key bits 60-63
-// when n <= 15: that inverse leads back to the state's parent, in the previous layer, so the
-// expansion skips it.  The visited set always holds untagged keys.
+// when the key leaves them free (n * width <= 60): that inverse leads back to the state's
+// parent, in the previous layer, so the expansion skips it.  The visited set always holds
+// untagged keys.
 constexpr uint64_t kKeyBits60 = (1ull << 60) - 1;
 
 constexpr int kVisitHash = 0;
@@ -60,6 +72,8 @@ struct alignas(128) JobDev {
     int use_start;             // 1: grow from start_key (a central state), 0: from the identity
     uint64_t bitmap_words;     // bitmap mode: 32-bit words in `table` (ceil(n!/32))
     uint64_t start_key;        // packed start vector when use_start
+    int tagged;                // 1: keys leave bits 60-63 free for the parent-edge tag
+    int pad1;
     // dynamic, updated between rounds by block 0
     alignas(128) unsigned long long lo;     // frontier = keys[lo, hi)
     unsigned long long hi;

@@ -181,8 +181,12 @@ uint64_t group_order_uncached(int n, int k, const uint8_t* gens) {
         }
         if (!restarted) --i;
     }
+    // saturating at 2^64 - 1 (S_21 and larger groups exceed 64 bits)
     uint64_t order = 1;
-    for (auto& L : C.lv) order *= (uint64_t)L.orbit.size();
+    for (auto& L : C.lv) {
+        const unsigned __int128 x = (unsigned __int128)order * L.orbit.size();
+        order = x > (unsigned __int128)~0ull ? ~0ull : (uint64_t)x;
+    }
     return order;
 }
 

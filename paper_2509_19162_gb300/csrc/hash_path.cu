@@ -221,7 +221,7 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
     const bool active = idx < hi;
     const int n = J->n;
     unsigned tag = 0;                       // 1 + generator that leads back to the parent
-    if (n <= 15) {
+    if (J->tagged) {
         tag = (unsigned)(s >> 60);
         s &= kKeyBits60;
     }
@@ -233,7 +233,7 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
         unsigned vmask = 0;
 #pragma unroll
         for (int i = 0; i < kProbeILP; ++i) {
-            t[i] = (i < ng) ? apply_gen(gens[g0 + i], s) : 0;
+            t[i] = (i < ng) ? apply_gen<kMode != kVisitBitmap>(gens[g0 + i], s) : 0;
             if (active && i < ng && tag != (unsigned)(g0 + i + 1)) vmask |= 1u << i;
         }
         if (kMode == kVisitBitmap)
@@ -254,7 +254,7 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
         for (int i = 0; i < kProbeILP; ++i) {
             const unsigned fresh = __ballot_sync(0xffffffffu, res[i] == 1);
             if (res[i] == 1) {
-                const uint64_t itag = (n <= 15 && i < ng) ? (uint64_t)gens[g0 + i].inv_tag << 60 : 0;
+                const uint64_t itag = (J->tagged && i < ng) ? (uint64_t)gens[g0 + i].inv_tag << 60 : 0;
                 buf[cnt + __popc(fresh & lanemask_lt())] = t[i] | itag;
             }
             cnt += __popc(fresh);

@@ -86,11 +86,11 @@ void dev_free(void* p, cudaStream_t st) {
 }
 
 // ---- generators -------------------------------------------------------------------------
-bool is_perm_row(const uint8_t* g, int n) {
-    unsigned seen = 0;
+bool is_perm_row(const uint8_t* g, int n) {   // n <= 64
+    uint64_t seen = 0;
     for (int i = 0; i < n; ++i) {
-        if (g[i] >= n || (seen >> g[i]) & 1u) return false;
-        seen |= 1u << g[i];
+        if (g[i] >= n || (seen >> g[i]) & 1ull) return false;
+        seen |= 1ull << g[i];
     }
     return true;
 }
@@ -101,20 +101,48 @@ bool is_identity_row(const uint8_t* g, int n) {
     return true;
 }
 
-// Shift-and-mask form of the gather t[i] = s[g[i]] (see GenSM).
-GenSM make_gensm(const uint8_t* g, int n) {
-    GenSM G;
+// Device form of the gather t[i] = s[g[i]] on keys of w-bit elements (see GenSM): shift-and-mask
+// terms, or, when those would be more than kMaxTerms, a range reversal if g reverses one
+// contiguous range of positions and fixes the rest.  Returns false if neither form fits.
+bool make_gensm_checked(const uint8_t* g, int n, int w, GenSM& G) {
     std::memset(&G, 0, sizeof(G));
-    for (int i = 0; i < n; ++i) {
-        const unsigned rot = (unsigned)((4 * (i - (int)g[i]) + 64) & 63);
+    G.width = (uint8_t)w;
+    const uint64_t elem_mask = (1ull << w) - 1;
+    bool fits = true;
+    for (int i = 0; i < n && fits; ++i) {
+        const unsigned rot = (unsigned)(((w * (i - (int)g[i])) % 64 + 64) & 63);
         uint32_t t = 0;
         while (t < G.nterms && G.rot[t] != rot) ++t;
         if (t == G.nterms) {
+            if (G.nterms == (uint32_t)cg::kMaxTerms) { fits = false; break; }
             G.rot[t] = (uint8_t)rot;
             G.nterms++;
         }
-        G.mask[t] |= 0xFull << (4 * i);
+        G.mask[t] |= elem_mask << (w * i);
     }
+    if (fits) return true;
+    int a = -1, b = -1;
+    for (int i = 0; i < n; ++i)
+        if (g[i] != i) {
+            if (a < 0) a = i;
+            b = i;
+        }
+    bool reversal = a >= 0 && b > a;
+    for (int i = a; reversal && i <= b; ++i) reversal = g[i] == a + b - i;
+    if (!reversal) return false;
+    std::memset(&G, 0, sizeof(G));
+    G.width = (uint8_t)w;
+    const int elems = 64 / w;   // after the bit reversal element e sits at elems - 1 - e
+    G.kind = 1;
+    G.rev_shift = (int16_t)(w * (elems - 1 - a - b));
+    const uint64_t lo = (uint64_t)w * a, hi = (uint64_t)w * (b + 1);
+    G.mask[0] = (hi >= 64 ? ~0ull : ((1ull << hi) - 1)) & ~((1ull << lo) - 1);
+    return true;
+}
+
+GenSM make_gensm(const uint8_t* g, int n, int w = 4) {
+    GenSM G;
+    make_gensm_checked(g, n, w, G);
     return G;
 }
 
@@ -132,9 +160,9 @@ std::vector<std::vector<uint8_t>> clean_rows(int n, int k, const uint8_t* gens) 
 
 // Shift-and-mask forms of distinct rows, with each generator's inverse tag (1 + index of its
 // inverse among the rows when that index is below 15, else 0).
-std::vector<GenSM> make_gensms(const std::vector<std::vector<uint8_t>>& rows, int n) {
+std::vector<GenSM> make_gensms(const std::vector<std::vector<uint8_t>>& rows, int n, int w = 4) {
     std::vector<GenSM> out;
-    for (auto& r : rows) out.push_back(make_gensm(r.data(), n));
+    for (auto& r : rows) out.push_back(make_gensm(r.data(), n, w));
     for (size_t j = 0; j < rows.size(); ++j) {
         std::vector<uint8_t> inv(n);
         for (int i = 0; i < n; ++i) inv[rows[j][i]] = (uint8_t)i;
@@ -154,8 +182,8 @@ bool closed_under_inverse(const std::vector<std::vector<uint8_t>>& rows, int n) 
     return true;
 }
 
-int validate(int n, int k, const uint8_t* gens) {
-    if (n < 1 || n > cg::kMaxN || k < 1 || gens == nullptr) return CG_EINVAL;
+int validate(int n, int k, const uint8_t* gens, int max_n = cg::kMaxN) {
+    if (n < 1 || n > max_n || k < 1 || gens == nullptr) return CG_EINVAL;
     for (int j = 0; j < k; ++j)
         if (!is_perm_row(gens + (size_t)j * n, n)) return CG_EINVAL;
     return CG_OK;
@@ -286,6 +314,8 @@ struct cg_growth {
     int grid_override = 0;
     int ilp_override = 0;
     int mode = -1;                               // visited set chosen at the first run
+    std::vector<std::vector<uint8_t>> rows;      // the distinct non-identity generators
+    int width = 4;                               // bits per element of the packed keys
     bool use_start = false;                      // grow from a central state instead of e
     uint64_t start_key = 0;
     bool start_is_perm = true;                   // the start vector has distinct entries
@@ -428,6 +458,7 @@ void fill_static(cg_growth* h, JobDev& J) {
     J.bitmap_words = h->mode == cg::kVisitBitmap ? bitmap_words(h->n) : 0;
     J.use_start = h->use_start ? 1 : 0;
     J.start_key = h->start_key;
+    J.tagged = h->n * h->width <= 60 ? 1 : 0;
 }
 
 int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
@@ -513,7 +544,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         e = bitmap ? cg::launch_rebuild_bitmap(h->d_keys, keep, reinterpret_cast<unsigned*>(h->d_table),
                                                bitmap_words(h->n), h->n, &h->d_ctl->err, grid_max, st)
                    : cg::launch_rebuild_table(h->d_keys, keep, h->d_table, h->table_slots - 1,
-                                              h->n <= 15 ? cg::kKeyBits60 : ~0ull, &h->d_ctl->err,
+                                              h->n * h->width <= 60 ? cg::kKeyBits60 : ~0ull, &h->d_ctl->err,
                                               grid_max, st);
         if (e != cudaSuccess) return cuda_rc(e);
         fill_static(h, J);
@@ -699,7 +730,7 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
         if (!h->d_count) return CG_ENOMEM;
     }
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
-    const int bits = 4 * h->n;
+    const int bits = h->width * h->n;
     int cur = 0, prev = 1, nxt = 2;
     uint64_t Fcur = 1, Fprev = 0;
     h->sort_layers.assign(1, 1);
@@ -794,14 +825,20 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
                      uint64_t mem_cap, cg_growth_t* out) {
     if (out == nullptr) return CG_EINVAL;
     *out = nullptr;
-    int rc = validate(n, k, gens);
+    // n > 16 only grows from a start vector of narrow values (cg_growth_set_start)
+    int rc = validate(n, k, gens, cg::kMaxElems);
     if (rc) return rc;
     auto rows = clean_rows(n, k, gens);
     if (inverse_closed && !closed_under_inverse(rows, n)) return CG_ENOTCLOSED;
+    for (auto& r : rows) {   // with one bit per element: more than 16 offsets need a reversal
+        GenSM G;
+        if (!make_gensm_checked(r.data(), n, 1, G)) return CG_EINVAL;
+    }
     cg_growth* h = new (std::nothrow) cg_growth();
     if (!h) return CG_ENOMEM;
     h->n = n;
     h->k = (int)rows.size();
+    h->rows = rows;
     h->gsm = make_gensms(rows, n);
     h->inverse_closed = inverse_closed ? 1 : 0;
     h->max_radius = max_radius < 0 ? -1 : max_radius;
@@ -817,13 +854,20 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
 int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
     if (!h) return CG_EINVAL;
     int count[16] = {0};
-    uint64_t key = 0;
+    int maxv = 0;
     if (start)
         for (int i = 0; i < h->n; ++i) {
             if (start[i] > 15) return CG_EINVAL;
             count[start[i]]++;
-            key |= (uint64_t)start[i] << (4 * i);
+            maxv = std::max(maxv, (int)start[i]);
         }
+    // Permutations keep 4 bits per element (the rank-indexed strategies read them); other
+    // vectors take the narrowest width that holds their values: binary vectors 1 bit.
+    bool distinct = true;
+    for (int v = 0; v < 16; ++v) distinct &= count[v] <= 1;
+    const bool is_perm = start && distinct && maxv < h->n;
+    const int w = is_perm ? 4 : maxv <= 1 ? 1 : maxv <= 3 ? 2 : 4;
+    if (start && h->n * w > 64) return CG_EINVAL;
     if (h->device >= 0) {                 // buffers were sized for the previous start
         h->release(nullptr);
         cudaStreamSynchronize(nullptr);
@@ -833,20 +877,30 @@ int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
         h->use_start = false;
         h->start_key = 0;
         h->start_is_perm = true;
+        h->width = 4;
+        h->gsm = make_gensms(h->rows, h->n, 4);
         h->states_bound = h->order;
         return CG_OK;
     }
+    uint64_t key = 0;
+    for (int i = 0; i < h->n; ++i) key |= (uint64_t)start[i] << (w * i);
     // The orbit of the start vector has at most as many states as the group, and at most as
-    // many as the distinct rearrangements of the vector (a multinomial coefficient).
-    uint64_t rearr = factorial(h->n);
-    bool perm = true;
+    // many as the distinct rearrangements of the vector (a multinomial coefficient), computed as
+    // a product of binomials, saturating at 2^64 - 1.
+    uint64_t rearr = 1;
+    int placed = 0;
     for (int v = 0; v < 16; ++v) {
-        rearr /= factorial(count[v]);
-        perm &= count[v] <= 1;
+        for (int j = 1; j <= count[v]; ++j) {   // rearr *= C(placed + j, j) / C(placed + j - 1, j - 1)
+            ++placed;
+            const unsigned __int128 x = (unsigned __int128)rearr * (unsigned)placed / (unsigned)j;
+            rearr = x > (unsigned __int128)~0ull ? ~0ull : (uint64_t)x;
+        }
     }
     h->use_start = true;
     h->start_key = key;
-    h->start_is_perm = perm;
+    h->start_is_perm = is_perm;
+    h->width = w;
+    h->gsm = make_gensms(h->rows, h->n, w);
     h->states_bound = std::min(h->order, rearr);
     return CG_OK;
 }
@@ -890,6 +944,7 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
     cudaStream_t st = (cudaStream_t)cuda_stream;
     h->have_last = false;
     std::memset(&h->stats, 0, sizeof(h->stats));
+    if (!h->use_start && h->n > cg::kMaxN) return CG_EINVAL;   // the identity needs 4-bit elements
     if (h->k == 0 || h->max_radius == 0) {  // trivial group or radius 0: only the identity
         *num_layers_out = 1;
         if (cap < 1) return CG_EINVAL;
@@ -958,12 +1013,14 @@ int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64
     *count_out = cnt;
     if (cap < cnt || (!keys_out && cnt > 0)) return CG_EINVAL;
     cudaError_t e = cudaMemcpy(keys_out, h->last_layer_ptr, cnt * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && h->n <= 15)   // strip the parent-edge tags of stored states
+    if (e == cudaSuccess && h->n * h->width <= 60)   // strip the parent-edge tags of stored states
         for (uint64_t i = 0; i < cnt; ++i) keys_out[i] &= cg::kKeyBits60;
     return cuda_rc(e);
 }
 
 uint64_t cg_growth_group_order(cg_growth_t h) { return h ? h->order : 0; }
+
+int cg_growth_key_width(cg_growth_t h) { return h ? h->width : 0; }
 
 const char* cg_last_error_detail(void) {
     if (g_last_cuda_error == cudaSuccess) return "";
@@ -1231,6 +1288,7 @@ void layout_wave(cg_batch* b, cg_batch::Wave& w, int lcap) {
         D.max_radius = J.max_radius;
         D.mode = J.mode;
         D.bitmap_words = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) : 0;
+        D.tagged = J.n <= 15 ? 1 : 0;
     }
 }
 
@@ -1718,6 +1776,7 @@ int server_admit(cg_server* s, cudaStream_t st) {
         D.max_radius = J.max_radius;
         D.mode = J.mode;
         D.bitmap_words = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) : 0;
+        D.tagged = J.n <= 15 ? 1 : 0;
         D.status = cg::kFresh;
         s->h_jobs[free_slot] = D;
         cudaError_t e;

@@ -165,6 +165,7 @@ extern "C" int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inve
     J.n = n;
     J.layers_cap = cg::kMaxLayers;
     J.max_radius = max_radius < 0 ? -1 : max_radius;
+    J.tagged = n <= 15 ? 1 : 0;
 
     // Everything the kernels read first is rewritten here: the visited table is emptied, the
     // control block zeroed, the job and generators uploaded.

@@ -107,16 +107,24 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* t
 }
 
 // ---- expand ------------------------------------------------------------------------------------
-// out[j*F + i] = gens[j](in[i]).
+// out[j*F + i] = gens[j](in[i]).  The generators are staged in shared memory when they fit in
+// kExpandSmem bytes, else read through L1.
+constexpr size_t kExpandSmem = 32 << 10;
+
+template <bool kSmem>
 __global__ void expand_all_kernel(const GenSM* __restrict__ gens, int k, const uint64_t* __restrict__ in,
                                   unsigned long long F, uint64_t* __restrict__ out) {
     extern __shared__ GenSM s_gens[];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) s_gens[j] = gens[j];
-    __syncthreads();
+    const GenSM* g = gens;
+    if (kSmem) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) s_gens[j] = gens[j];
+        __syncthreads();
+        g = s_gens;
+    }
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < F; i += stride) {
         const uint64_t s = in[i];
-        for (int j = 0; j < k; ++j) out[(unsigned long long)j * F + i] = apply_gen(s_gens[j], s);
+        for (int j = 0; j < k; ++j) out[(unsigned long long)j * F + i] = apply_gen(g[j], s);
     }
 }
 
@@ -337,7 +345,11 @@ cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, un
     if (F == 0) return cudaSuccess;
     unsigned long long blocks = (F + kBlock - 1) / kBlock;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
-    expand_all_kernel<<<(unsigned)blocks, kBlock, sizeof(GenSM) * k, st>>>(d_gens, k, in, F, out);
+    const size_t smem = sizeof(GenSM) * (size_t)k;
+    if (smem <= kExpandSmem)
+        expand_all_kernel<true><<<(unsigned)blocks, kBlock, smem, st>>>(d_gens, k, in, F, out);
+    else
+        expand_all_kernel<false><<<(unsigned)blocks, kBlock, 0, st>>>(d_gens, k, in, F, out);
     return cudaGetLastError();
 }
 

@@ -131,7 +131,7 @@ __device__ __forceinline__ void sweep_state(const GenSM* gens, int k, unsigned* 
         unsigned old[kILP];
 #pragma unroll
         for (int i = 0; i < kILP; ++i)
-            if (active && g0 + i < k) rt[i] = pos_rank<kN>(apply_gen(gens[g0 + i], s));
+            if (active && g0 + i < k) rt[i] = pos_rank<kN>(apply_gen<false>(gens[g0 + i], s));
 #pragma unroll
         for (int i = 0; i < kILP; ++i)
             if (active && g0 + i < k) old[i] = atomicOr(V + (rt[i] >> 5), 1u << (unsigned)(rt[i] & 31u));

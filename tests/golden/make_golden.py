@@ -26,6 +26,9 @@ CASES = {
     # oracle B (visited bitmap over all n! ranks): the layers oracle A cannot hold in memory
     "s14_pancake_layers_b": (14, w.pancake(14), "bitmap", 10,
                              "S_14, 13 prefix reversals, layers 0..10 from the identity"),
+    # oracle C (visited set and layers as bitmaps over all n! ranks): whole growths of S_13
+    "s13_pancake_growth": (13, w.pancake(13), "bitmask", -1,
+                           "S_13, 12 prefix reversals, full growth from the identity"),
 }
 
 
@@ -34,13 +37,17 @@ def write(name):
     t0 = time.time()
     if two == "bitmap":
         g, rc = oracle.growth_bitmap(n, gens, max_radius=maxr)
+    elif two == "bitmask":
+        g, rc = oracle.growth_bitmask(n, gens, max_radius=maxr,
+                                      progress=lambda r, c: print(f"  layer {r}: {c}", flush=True))
     else:
         g, rc = oracle.growth(n, gens, two_layer=two, max_radius=maxr)
     dt = time.time() - t0
     path = os.path.join(HERE, name + ".txt")
     with open(path, "w") as f:
         f.write(f"# {desc}\n")
-        mode = "rank-bitmap oracle B" if two == "bitmap" else ("two-layer" if two else "full visited")
+        mode = {"bitmap": "rank-bitmap oracle B", "bitmask": "layer-bitmap oracle C"}.get(
+            two, "two-layer" if two else "full visited")
         f.write(f"# written by tests/golden/make_golden.py from the CPU oracle "
                 f"({mode} mode, max_radius={maxr}, {dt:.0f} s)\n")
         for r, c in enumerate(g):

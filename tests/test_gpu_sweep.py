@@ -202,3 +202,11 @@ def test_perm_rank_large_n(cg, n):
     assert ranks[0] == math.factorial(n) - 1 and ranks[1] == 0     # identity, full reversal
     assert all(r == _rank_by_definition(p) for p, r in zip(perms, ranks))
     assert np.array_equal(d_back.cpu().numpy().view(np.uint64), keys)
+
+
+@pytest.mark.parametrize("strategy", ["sweep", "bitmap"])
+def test_whole_s13_pancake_vs_oracle_c(cg, strategy):
+    # all 13! states; the 16 layers stored from the layer-bitmap CPU oracle (oracle C)
+    r = cg.growth(13, w.pancake(13), strategy=strategy)
+    assert r.status == 0
+    assert r.layers == golden("s13_pancake_growth")

@@ -31,7 +31,8 @@ def _apsp_coset_growth(n, gens, start):
     """Sphere sizes around `start` in the explicit graph on all distinct rearrangements of it."""
     from scipy.sparse import csr_matrix
     from scipy.sparse.csgraph import shortest_path
-    verts = sorted(set(itertools.permutations(start)))
+    from sympy.utilities.iterables import multiset_permutations
+    verts = sorted(tuple(v) for v in multiset_permutations(list(start)))
     index = {v: i for i, v in enumerate(verts)}
     rows, cols = [], []
     for v in verts:
@@ -92,7 +93,7 @@ def test_bin_transposons_and_reversals(n):
     assert sum(t) == math.comb(n, n // 2)
 
 
-@pytest.mark.parametrize("n", range(6, 17, 2))
+@pytest.mark.parametrize("n", list(range(6, 17, 2)) + [18, 20])
 def test_bin_lrx_gods_number_even_n(n):
     g, _ = oracle.growth(n, w.lrx(n), start=w.binary_start(n))
     assert len(g) - 1 == (n * (3 * n - 4) + 32 - 2 * (n % 4)) // 16
@@ -105,7 +106,8 @@ def test_bin_pancake_gods_number_even_n(n):
     assert len(g) - 1 == n - 1
 
 
-@pytest.mark.parametrize("n,want", [(12, 12 * 12 // 12 + 1), (13, (13 * 13 + 4 * 13 - 5) // 12)])
+@pytest.mark.parametrize("n,want", [(12, 12 * 12 // 12 + 1), (13, (13 * 13 + 4 * 13 - 5) // 12),
+                                    (18, 18 * 18 // 12 + 1), (19, (19 * 19 + 4 * 19 - 5) // 12)])
 def test_bin_consecutive_4cycles_gods_number(n, want):
     g, _ = oracle.growth(n, w.consecutive_4cycles(n), start=w.binary_start(n))
     assert len(g) - 1 == want
@@ -163,3 +165,20 @@ def test_coxeter_on_multiset_is_q_multinomial(counts):
     start = [v for v, c in enumerate(counts) for _ in range(c)]
     n = len(start)
     assert oracle.growth(n, w.coxeter(n), start=start)[0] == q_multinomial(counts)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_long_vectors_equal_all_pairs_shortest_paths(seed):
+    # n > 16: the oracle's 256-bit keys; vectors of two or three values, explicit graph by scipy
+    rng = np.random.default_rng(6000 + seed)
+    n = int(rng.integers(17, 21))
+    nvals = 2 if seed % 2 == 0 else 3
+    counts = [n - 2 * (nvals - 1)] + [2] * (nvals - 1)      # few rearrangements: small graph
+    start = [v for v, c in enumerate(counts) for _ in range(c)]
+    rng.shuffle(start)
+    start = [int(x) for x in start]
+    gens = w.random_perms(rng, n, 2)
+    if seed % 4 < 2:
+        gens = w.inverse_closure(gens)
+    g, rc = oracle.growth(n, gens, start=start)
+    assert rc == 0 and g == _apsp_coset_growth(n, gens, start)

@@ -298,3 +298,39 @@ def test_stored_values_of_both_oracles_agree():
     b = read("s14_pancake_layers_b.txt")     # oracle B, layers 0..10
     assert len(a) == 9 and len(b) == 11 and b[:9] == a
     assert b[10] > 2 ** 31 >= max(b[:10])     # config 3 stops after layer 10
+
+
+# ---- oracle C (visited set and layers as bitmaps over all n! ranks) is pinned to A and B ----
+
+@pytest.mark.parametrize("family", ["coxeter", "lrx", "lx", "pancake", "reversals", "star",
+                                    "three_cycles", "prefix_cycles", "all_transpositions"])
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_oracle_c_equals_oracle_a_on_families(family, n):
+    gens = w.FAMILIES[family](n)
+    if not gens:
+        pytest.skip("empty set")
+    assert oracle.growth_bitmask(n, gens, threads=3) == oracle.growth(n, gens)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_oracle_c_equals_oracle_a_random(seed):
+    rng = np.random.default_rng(1900 + seed)
+    n = int(rng.integers(3, 10))
+    gens = w.random_perms(rng, n, int(rng.integers(1, 4)))
+    if seed % 2:
+        gens = w.inverse_closure(gens)
+    assert oracle.growth_bitmask(n, gens, threads=1 + seed % 4) == oracle.growth(n, gens)
+
+
+def test_oracle_c_limits_closed_forms_and_progress():
+    assert oracle.growth_bitmask(9, w.coxeter(9))[0] == mahonian(9)
+    c = stirling1_unsigned(8)
+    assert oracle.growth_bitmask(8, w.all_transpositions(8))[0] == [c[8 - r] for r in range(8)]
+    g, rc = oracle.growth_bitmask(9, w.coxeter(9), max_radius=6)
+    assert rc == 1 and g == mahonian(9)[:7]
+    g, rc = oracle.growth_bitmask(9, w.coxeter(9), stop_above=5000)
+    assert rc == 1 and g == mahonian(9)[:len(g)] and g[-1] > 5000
+    seen = []
+    oracle.growth_bitmask(7, w.pancake(7), progress=lambda r, s: seen.append((r, s)))
+    assert [s for _, s in seen] == oracle.growth(7, w.pancake(7))[0][1:]
+    assert oracle.growth_bitmask(10, w.lrx(10), max_radius=12) == oracle.growth_bitmap(10, w.lrx(10), max_radius=12)
