@@ -172,10 +172,15 @@ def get_workload(name):
     if name == "s14_pancake":
         return wl.config_s14_pancake()
     if ":" in name:
-        # any named family, full growth: e.g. "pancake:14" (the whole of S_14), "coxeter:13"
-        fam, n = name.split(":")
-        n = int(n)
+        # any named family, full growth: e.g. "pancake:14" (the whole of S_14), "coxeter:13";
+        # a third field "bin" grows the orbit of the binary vector 0^(n/2) 1^(n - n/2) (the
+        # "Bin" Schreier coset graph), e.g. "lrx:32:bin"
+        parts = name.split(":")
+        fam, n = parts[0], int(parts[1])
         gens = wl.FAMILIES[fam](n)
+        if len(parts) > 2 and parts[2] == "bin":
+            return wl.GrowthJob(n, gens, wl.is_inverse_closed(gens), name=f"Bin{n}-{fam}-k{len(gens)}-full",
+                                family=fam, start=wl.binary_start(n))
         return wl.GrowthJob(n, gens, wl.is_inverse_closed(gens), name=f"S{n}-{fam}-k{len(gens)}-full",
                             family=fam)
     raise ValueError(name)
@@ -193,7 +198,7 @@ REFERENCE_STEP_RADIUS = {"s11_lrx": 28, "s8_coxeter": -1, "s14_pancake": 5}
 def oracle_sample(job, radius):
     import oracle
     t0 = time.perf_counter()
-    layers, rc = oracle.growth(job.n, job.gens, max_radius=radius)
+    layers, rc = oracle.growth(job.n, job.gens, max_radius=radius, start=job.start)
     dt = time.perf_counter() - t0
     complete = (rc == 0)
     return neighbours(layers, job.k, complete), dt, layers, complete
@@ -206,7 +211,7 @@ def sample_radius(job, budget_s):
     R = 1
     while True:
         t0 = time.perf_counter()
-        _, rc = oracle.growth(job.n, job.gens, max_radius=R)
+        _, rc = oracle.growth(job.n, job.gens, max_radius=R, start=job.start)
         if rc == 0:
             return -1
         if time.perf_counter() - t0 > budget_s / 4:
@@ -273,7 +278,8 @@ def run_ours(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
 
     handle = cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
-                       stop_above=job.stop_above, keep_last=False, strategy=args.strategy)
+                       stop_above=job.stop_above, keep_last=False, strategy=args.strategy,
+                       start=job.start)
     # warm-up (also allocates the job's buffers: inputs resident before the timed region)
     res = None
     for _ in range(args.warmup):
@@ -333,7 +339,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
-                       stop_above=job.stop_above, strategy=args.strategy) as g:
+                       stop_above=job.stop_above, strategy=args.strategy, start=job.start) as g:
             r = g.run(stream)
             st = g.stats()
         e2e_times.append(time.perf_counter() - t0)

@@ -43,6 +43,7 @@ class GrowthJob:
     family: str = ""
     arrival: float = 0.0          # serving only: arrival time in units of 1/rate
     extra: dict = field(default_factory=dict)
+    start: Optional[List[int]] = None   # central state of a Schreier coset graph (None: identity)
 
     @property
     def k(self) -> int:
