@@ -307,9 +307,12 @@ def run_ours(args):
     st0 = handle.stats()
     strat_name = {1: "hash", 2: "sort", 3: "bitmap", 4: "sweep"}.get(st0["strategy_used"], "?")
     variant = st0["probe_variant"]
+    # kernel names as ncu prints them: the single-job bitmap kernel with one generator in
+    # flight is compiled per n (last template argument), every other variant has 0 there
+    per_n = job.n if (strat_name == "bitmap" and variant == 17 and 2 <= job.n <= 14) else 0
     kernel_name = {"sort": "radix sort / merge-path kernels",
-                   "sweep": f"sweep_grow_kernel<{variant}>"}.get(
-        strat_name, f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 0>")
+                   "sweep": f"sweep_grow_kernel<{min(variant, 2)}, {job.n}>"}.get(
+        strat_name, f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 0, {per_n}>")
     for i in range(args.steps):
         flush.zero_()                               # evict L2 between timed steps
         torch.cuda.synchronize()
@@ -491,9 +494,9 @@ def run_batch(args):
                    "parallelism": "groups sharded over ranks" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1>",
+                     "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0>",
                                                  f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}"),
-                     "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1> (multi-job, "
+                     "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0> (multi-job, "
                                f"{launches // (3 * args.steps)} launches per batch run)",
                      "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind},
         "e2e": {"value": nb_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": est["h2d_bytes"],

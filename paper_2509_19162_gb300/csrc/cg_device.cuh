@@ -213,6 +213,33 @@ __device__ __forceinline__ void table_insert_multi_slot(uint64_t* table, uint64_
 // onto [0, n!): digit c_i = number of elements after position i that are smaller than p[i],
 // i.e. p[i] minus the smaller values already used; rank = sum c_i (n-1-i)!, evaluated in
 // Horner form.
+// The same rank with n known at compile time (N > 0): the loop unrolls with constant digit
+// positions and multipliers.
+template <int N>
+__device__ __forceinline__ uint64_t perm_rank_n(uint64_t key) {
+    unsigned used = 0;
+    if (N <= 12) {
+        unsigned r = 0;
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) {
+            const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+            const unsigned c = v - __popc(used & ((1u << v) - 1u));
+            used |= 1u << v;
+            r = r * (unsigned)(N - i) + c;
+        }
+        return r;
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i) {
+        const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
+        const unsigned c = v - __popc(used & ((1u << v) - 1u));
+        used |= 1u << v;
+        r = r * (uint64_t)(N - i) + c;
+    }
+    return r;
+}
+
 __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
     // The last digit is always 0 and is skipped; the loop is unrolled so every nibble shift is
     // a constant.  For n <= 12 the rank fits in 32 bits.
@@ -247,7 +274,7 @@ __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
 // atomicOr per key, whose returned word says whether the bit was already set (a single L2
 // round trip whether the key is new or not).  res[i] = 1 if this call set the bit, 0 if it
 // was set, -1 if the rank fell outside the bitmap (not a permutation of 0..n-1).
-template <int G>
+template <int G, int N = 0>
 __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words, int n,
                                                     const uint64_t (&key)[G], int (&res)[G],
                                                     unsigned vmask) {
@@ -256,7 +283,7 @@ __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         res[i] = 0;
-        const uint64_t r = perm_rank(key[i], n);
+        const uint64_t r = N > 0 ? perm_rank_n<(N > 0 ? N : 1)>(key[i]) : perm_rank(key[i], n);
         w[i] = r >> 5;
         bit[i] = 1u << (unsigned)(r & 31u);
         if ((vmask >> i & 1u) && w[i] >= words) res[i] = -1;

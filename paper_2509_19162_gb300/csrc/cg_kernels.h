@@ -18,9 +18,10 @@ cudaError_t launch_init_jobs(JobDev* d_jobs, int njobs, unsigned long long* d_ub
                              cudaStream_t st, int only_fresh = 0);
 cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                                 cudaStream_t st);
+// n > 0: the jobs' n, for the kernel variants compiled per n (a single rank-bitmap job).
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              int grid, int max_rounds, uint64_t timeout_ns, int ilp,
-                             cudaStream_t st);
+                             cudaStream_t st, int n = 0);
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,
                                  uint64_t mask, uint64_t key_mask, int* d_err, int grid,
                                  cudaStream_t st);

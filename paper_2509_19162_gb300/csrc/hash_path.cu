@@ -13,6 +13,7 @@
 // needs; for an inverse-closed set it is a superset of the two layers that suffice.
 #include <cooperative_groups.h>
 #include <cstdio>
+#include <utility>
 
 #include "cg_device.cuh"
 #include "cg_kernels.h"
@@ -214,7 +215,7 @@ __device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDe
 // One unit = 32 frontier states (one per lane) of job J, every generator applied to each:
 // expand, insert-if-absent into the visited table, stage the winners.  kProbeILP generators
 // are handled together (that many independent probe sequences in flight per thread).
-template <int kProbeILP, int kMode>
+template <int kProbeILP, int kMode, int kN = 0>
 __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned long long idx,
                                         unsigned long long hi, uint64_t* buf, int& cnt, int lane,
                                         bool& overflow_seen, uint64_t s) {
@@ -237,8 +238,8 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
             if (active && i < ng && tag != (unsigned)(g0 + i + 1)) vmask |= 1u << i;
         }
         if (kMode == kVisitBitmap)
-            bitmap_insert_multi<kProbeILP>(reinterpret_cast<unsigned*>(J->table), J->bitmap_words,
-                                           n, t, res, vmask);
+            bitmap_insert_multi<kProbeILP, kN>(reinterpret_cast<unsigned*>(J->table), J->bitmap_words,
+                                               n, t, res, vmask);
         else if (kMode == 1)
             table_insert_multi_sector<kProbeILP>(J->table, J->table_mask, t, res, vmask, kMaxProbe);
         else
@@ -275,7 +276,7 @@ __device__ __forceinline__ unsigned long long draw_unit(unsigned long long& coun
 // from `s_unit` (set to b0 by the caller, followed by __syncthreads).  Ends with the block's
 // flush of newly found states.  The next unit's frontier key is loaded while the current unit
 // is processed.
-template <int kProbeILP, int kMode>
+template <int kProbeILP, int kMode, int kN = 0>
 __device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsigned long long& s_unit,
                                              unsigned long long ue, uint64_t* buf, int lane) {
     const unsigned long long lo = ld_relaxed_ull(&J->lo);
@@ -289,7 +290,7 @@ __device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsig
         const uint64_t s_cur = s_next;
         const unsigned long long nb = draw_unit(s_unit, lane);
         s_next = (nb < ue && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
-        do_unit<kProbeILP, kMode>(J, gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen, s_cur);
+        do_unit<kProbeILP, kMode, kN>(J, gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen, s_cur);
         // Stop early once any warp found the job's buffers full (the layer will be redone after
         // the host grows them).
         if ((++iter & 3u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
@@ -308,7 +309,7 @@ constexpr int kSmemGens = 32;
 
 // kMulti = false: the launch has exactly one job (the single-job path only is compiled, which
 // keeps registers low); true: any number of jobs.
-template <int kProbeILP, int kMode, bool kMulti>
+template <int kProbeILP, int kMode, bool kMulti, int kN = 0>
 __global__ void __launch_bounds__(kGrowBlock, kMode == 2 ? 4 : ((kMode == 1 && kProbeILP >= 3) ? 2 : 3))
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
                  uint64_t timeout_ns) {
@@ -333,8 +334,8 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         bool overflow_seen = false;
         if (!kMulti) {
             // One job: each block takes a contiguous range of the round's units.
-            phase_single<kProbeILP, kMode>(jobs, single_gens, s_unit, total * (blockIdx.x + 1) / gridDim.x,
-                                           buf, lane);
+            phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, total * (blockIdx.x + 1) / gridDim.x,
+                                               buf, lane);
         } else {
             int cur = -1;
             JobDev* J = nullptr;
@@ -376,7 +377,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     ++round;
                     if (threadIdx.x == 0) s_unit = 0;
                     __syncthreads();
-                    phase_single<kProbeILP, kMode>(jobs, single_gens, s_unit, t, buf, lane);
+                    phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, t, buf, lane);
                     __syncthreads();
                     close_round_single(jobs, ubeg, ctl);
                 }
@@ -521,6 +522,21 @@ GrowFn grow_fn_t(int variant) {
 }
 
 GrowFn grow_fn(int variant, bool multi) { return multi ? grow_fn_t<true>(variant) : grow_fn_t<false>(variant); }
+
+// The single-job rank-bitmap kernel with one generator in flight per thread (the default for
+// S_n, n <= 14) is also compiled per n, so its rank arithmetic unrolls with constants.
+template <int... Ns>
+GrowFn grow_fn_bitmap_n(int n, std::integer_sequence<int, Ns...>) {
+    GrowFn f = nullptr;
+    (void)((n == Ns + 2 ? (f = hash_grow_kernel<1, 2, false, Ns + 2>, 0) : 0) + ...);
+    return f;
+}
+
+GrowFn grow_fn(int variant, bool multi, int n) {
+    if (variant == 17 && !multi && n >= 2 && n <= 14)
+        return grow_fn_bitmap_n(n, std::make_integer_sequence<int, 13>{});
+    return grow_fn(variant, multi);
+}
 }  // namespace
 
 int hash_grow_max_grid(int device, int ilp, bool multi) {
@@ -548,7 +564,8 @@ cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d
 }
 
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
-                             int grid, int max_rounds, uint64_t timeout_ns, int ilp, cudaStream_t st) {
+                             int grid, int max_rounds, uint64_t timeout_ns, int ilp, cudaStream_t st,
+                             int n) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -560,7 +577,7 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, njobs > 1), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
+    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, njobs > 1, n), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
                               timeout_ns);
 }
 
