@@ -47,15 +47,17 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def measured_traffic(kernel_name, workload):
+def measured_traffic(kernel_name, workload, settings=None):
     """DRAM bytes per launch of `kernel_name` on `workload` from the committed ncu record
-    (profiles/traffic.json), or None when there is none or the kernel's sources changed since it
-    was taken."""
+    (profiles/traffic.json), or None when there is none, the kernel's sources changed since it
+    was taken, or it was taken under other launch settings."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel_name)
         if not rec or rec.get("workload") != workload:
+            return None
+        if "settings" in rec and rec["settings"] != (settings or rec["settings"]):
             return None
         h = hashlib.sha256()
         for src in rec["kernel_sources"]:
@@ -495,7 +497,8 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0>",
-                                                 f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}"),
+                                                 f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}",
+                                                 tuned["settings"] if tuned else None),
                      "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0> (multi-job, "
                                f"{launches // (3 * args.steps)} launches per batch run)",
                      "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind},
