@@ -116,6 +116,12 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
 
 // close_round for a launch with one job, by one thread (no block-wide scan).  Called by every
 // thread of the closing block.
+// Units of a single-job round handed out in equal contiguous ranges per block; the rest (a
+// quarter) is drawn dynamically by the blocks that finish first.
+__host__ __device__ __forceinline__ unsigned long long static_units(unsigned long long total) {
+    return total - total / 4;
+}
+
 __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl) {
     if (threadIdx.x == 0) {
         JobDev& J = jobs[0];
@@ -146,6 +152,7 @@ __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* 
         ubeg[0] = 0;
         ubeg[1] = units;
         *(volatile unsigned long long*)&ctl->total_units = units;
+        *(volatile unsigned long long*)&ctl->dyn_next = static_units(units);
         *(volatile int*)&ctl->rounds += 1;   // one closing thread at a time
         // After the caller's __syncthreads, this fence makes the block's new states and the
         // job's new frontier visible device-wide before the next round reads them via L2.
@@ -278,18 +285,38 @@ __device__ __forceinline__ unsigned long long draw_unit(unsigned long long& coun
 // is processed.
 template <int kProbeILP, int kMode, int kN = 0>
 __device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsigned long long& s_unit,
-                                             unsigned long long ue, uint64_t* buf, int lane) {
+                                             unsigned long long ue, unsigned long long total,
+                                             unsigned long long* dyn, uint64_t* buf, int lane) {
     const unsigned long long lo = ld_relaxed_ull(&J->lo);
     const unsigned long long hi = ld_relaxed_ull(&J->hi);
     int cnt = 0;
     bool overflow_seen = false;
     unsigned iter = 0;
-    unsigned long long b = draw_unit(s_unit, lane);
-    uint64_t s_next = (b < ue && lo + (b << 5) + lane < hi) ? __ldcg(J->keys + lo + (b << 5) + lane) : 0;
-    while (b < ue) {
+    // The block's own range [.., ue) first; then units of the shared tail, two per draw from
+    // the global counter `dyn` (nullptr: no shared tail, e.g. when one block runs the round).
+    unsigned long long pending = ~0ull;
+    auto next_unit = [&]() -> unsigned long long {
+        const unsigned long long u = draw_unit(s_unit, lane);
+        if (u < ue) return u;
+        if (pending != ~0ull) {
+            const unsigned long long p = pending;
+            pending = ~0ull;
+            return p;
+        }
+        if (dyn == nullptr) return ~0ull;
+        unsigned long long d = 0;
+        if (lane == 0) d = atomicAdd(dyn, 2ull);
+        d = __shfl_sync(0xffffffffu, d, 0);
+        if (d >= total) return ~0ull;
+        if (d + 1 < total) pending = d + 1;
+        return d;
+    };
+    unsigned long long b = next_unit();
+    uint64_t s_next = (b != ~0ull && lo + (b << 5) + lane < hi) ? __ldcg(J->keys + lo + (b << 5) + lane) : 0;
+    while (b != ~0ull) {
         const uint64_t s_cur = s_next;
-        const unsigned long long nb = draw_unit(s_unit, lane);
-        s_next = (nb < ue && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
+        const unsigned long long nb = next_unit();
+        s_next = (nb != ~0ull && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
         do_unit<kProbeILP, kMode, kN>(J, gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen, s_cur);
         // Stop early once any warp found the job's buffers full (the layer will be redone after
         // the host grows them).
@@ -328,14 +355,17 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
     for (int round = 0; round < max_rounds; ++round) {
         const unsigned long long total = ld_relaxed_ull(&ctl->total_units);
         if (total == 0) break;
-        if (threadIdx.x == 0) s_unit = total * blockIdx.x / gridDim.x;   // this block's first unit
+        // Rounds of at least 16 units per block share their last quarter (blocks that finish
+        // their range early take from it); smaller rounds are split in equal ranges only.
+        const bool shared_tail = !kMulti && total >= 16ull * gridDim.x;
+        const unsigned long long stat = shared_tail ? static_units(total) : total;
+        if (threadIdx.x == 0) s_unit = stat * blockIdx.x / gridDim.x;   // this block's first unit
         __syncthreads();
         int cnt = 0;
         bool overflow_seen = false;
         if (!kMulti) {
-            // One job: each block takes a contiguous range of the round's units.
-            phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, total * (blockIdx.x + 1) / gridDim.x,
-                                               buf, lane);
+            phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, stat * (blockIdx.x + 1) / gridDim.x,
+                                               total, shared_tail ? &ctl->dyn_next : nullptr, buf, lane);
         } else {
             int cur = -1;
             JobDev* J = nullptr;
@@ -377,7 +407,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     ++round;
                     if (threadIdx.x == 0) s_unit = 0;
                     __syncthreads();
-                    phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, t, buf, lane);
+                    phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, t, t, nullptr, buf, lane);
                     __syncthreads();
                     close_round_single(jobs, ubeg, ctl);
                 }
@@ -426,6 +456,7 @@ __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* u
     }
     ubeg[njobs] = acc;
     ctl->total_units = acc;
+    ctl->dyn_next = static_units(acc);
     ctl->rounds = 0;
     ctl->bar_count = 0;
     ctl->bar_gen = 0;
