@@ -43,6 +43,12 @@ __device__ __forceinline__ int find_job(const unsigned long long* ubeg, int njob
     return lo;
 }
 
+// Units of a round handed out in equal contiguous ranges per block; the rest (a quarter) is
+// drawn dynamically by the blocks that finish first.
+__host__ __device__ __forceinline__ unsigned long long static_units(unsigned long long total) {
+    return total - total / 4;
+}
+
 // Phase B, executed by the block that arrives last at the round's barrier: close the layer of
 // every running job and lay out the work of the next round.  ubeg has njobs + 1 entries.
 __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl) {
@@ -110,17 +116,13 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
     if (threadIdx.x == 0) {
         ubeg[njobs] = s_carry;
         ctl->total_units = s_carry;
+        ctl->dyn_next = static_units(s_carry);
         atomicAdd(&ctl->rounds, 1);
     }
 }
 
 // close_round for a launch with one job, by one thread (no block-wide scan).  Called by every
 // thread of the closing block.
-// Units of a single-job round handed out in equal contiguous ranges per block; the rest (a
-// quarter) is drawn dynamically by the blocks that finish first.
-__host__ __device__ __forceinline__ unsigned long long static_units(unsigned long long total) {
-    return total - total / 4;
-}
 
 __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl) {
     if (threadIdx.x == 0) {
@@ -357,7 +359,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         if (total == 0) break;
         // Rounds of at least 16 units per block share their last quarter (blocks that finish
         // their range early take from it); smaller rounds are split in equal ranges only.
-        const bool shared_tail = !kMulti && total >= 16ull * gridDim.x;
+        const bool shared_tail = total >= 16ull * gridDim.x;
         const unsigned long long stat = shared_tail ? static_units(total) : total;
         if (threadIdx.x == 0) s_unit = stat * blockIdx.x / gridDim.x;   // this block's first unit
         __syncthreads();
@@ -370,8 +372,26 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
             int cur = -1;
             JobDev* J = nullptr;
             unsigned long long lo = 0, hi = 0, u0 = 0;
-            const unsigned long long ue = total * (blockIdx.x + 1) / gridDim.x;
-            for (unsigned long long u = draw_unit(s_unit, lane); u < ue; u = draw_unit(s_unit, lane)) {
+            const unsigned long long ue = stat * (blockIdx.x + 1) / gridDim.x;
+            unsigned long long pending = ~0ull;
+            // the block's range, then (large rounds) the shared tail, two units per draw
+            auto next_unit = [&]() -> unsigned long long {
+                const unsigned long long u = draw_unit(s_unit, lane);
+                if (u < ue) return u;
+                if (pending != ~0ull) {
+                    const unsigned long long p = pending;
+                    pending = ~0ull;
+                    return p;
+                }
+                if (!shared_tail) return ~0ull;
+                unsigned long long d = 0;
+                if (lane == 0) d = atomicAdd(&ctl->dyn_next, 2ull);
+                d = __shfl_sync(0xffffffffu, d, 0);
+                if (d >= total) return ~0ull;
+                if (d + 1 < total) pending = d + 1;
+                return d;
+            };
+            for (unsigned long long u = next_unit(); u != ~0ull; u = next_unit()) {
                 const int j = find_job(ubeg, njobs, u);
                 if (j != cur) {
                     if (J) stage_flush(buf, cnt, J, lane);
