@@ -128,7 +128,7 @@ struct alignas(128) Ctl {
     unsigned long long total_units; // warp work units of the current round
     unsigned int pad2[28];
     // A round's units split into a static part, in equal contiguous ranges per block, and the
-    // last quarter, which blocks that finish their range draw from this counter (single job).
+    // second half, which blocks that finish their range draw from this counter.
     unsigned long long dyn_next;
     unsigned int pad3[30];
     struct alignas(128) Group {
