@@ -1,6 +1,7 @@
 // Internal types shared by the host driver and the kernels of the growth library.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -83,6 +84,12 @@ struct alignas(128) JobDev {
     int overflow;              // set during a round: keys or table ran out
     int pad;
 };
+// The round close loads (lo, hi) and (tail, radius | status << 32) as two 16-byte vectors.
+static_assert(offsetof(JobDev, lo) % 16 == 0 && offsetof(JobDev, hi) == offsetof(JobDev, lo) + 8,
+              "JobDev: lo, hi must form one aligned 16-byte vector");
+static_assert(offsetof(JobDev, tail) % 16 == 0 && offsetof(JobDev, radius) == offsetof(JobDev, tail) + 8 &&
+                  offsetof(JobDev, status) == offsetof(JobDev, radius) + 4,
+              "JobDev: tail, radius, status must form one aligned 16-byte vector");
 
 // One growth of the sweep strategy: the visited set and the last three layers are bitmaps over
 // the position-major Lehmer ranks 0..n!-1 (one bit per element of S_n).  Layer r lives in

@@ -127,35 +127,44 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
 __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl) {
     if (threadIdx.x == 0) {
         JobDev& J = jobs[0];
-        volatile JobDev& V = jobs[0];
+        // The round's state in one round trip: (lo, hi), (tail, radius | status << 32), overflow
+        // and the static limits are loaded together; nothing is read back after a write.
+        unsigned long long lo, hi, tail, rs;
+        asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(&J.lo));
+        asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(tail), "=l"(rs) : "l"(&J.tail));
+        const int overflow = ld_relaxed_int(&J.overflow);
+        const int max_radius = J.max_radius, layers_cap = J.layers_cap;
+        const uint64_t stop_above = J.stop_above;
+        int radius = (int)(unsigned)(rs & 0xffffffffull);
+        int status = (int)(unsigned)(rs >> 32);
         unsigned long long units = 0;
-        if (V.status == kRunning) {
-            const unsigned long long tail = ld_relaxed_ull(&J.tail);
-            const unsigned long long hi = V.hi;
-            if (ld_relaxed_int(&J.overflow)) {
-                V.status = kNeedMem;
+        if (status == kRunning) {
+            volatile JobDev& V = jobs[0];
+            if (overflow) {
+                status = kNeedMem;
             } else {
                 const unsigned long long fresh = tail - hi;
                 if (fresh == 0) {
-                    V.status = kDone;
+                    status = kDone;
                 } else {
-                    const int r = V.radius + 1;
-                    J.layer_sizes[r] = fresh;
-                    V.radius = r;
+                    radius += 1;
+                    J.layer_sizes[radius] = fresh;
+                    V.radius = radius;
                     V.lo = hi;
                     V.hi = tail;
-                    if (J.max_radius >= 0 && r >= J.max_radius) V.status = kTruncRadius;
-                    else if (J.stop_above > 0 && fresh > J.stop_above) V.status = kTruncAbove;
-                    else if (r + 1 >= J.layers_cap) V.status = kTruncRadius;
+                    if (max_radius >= 0 && radius >= max_radius) status = kTruncRadius;
+                    else if (stop_above > 0 && fresh > stop_above) status = kTruncAbove;
+                    else if (radius + 1 >= layers_cap) status = kTruncRadius;
+                    if (status == kRunning) units = (fresh + 31) >> 5;
                 }
             }
-            if (V.status == kRunning) units = (tail - hi + 31) >> 5;
+            if (status != kRunning) V.status = status;
         }
         ubeg[0] = 0;
         ubeg[1] = units;
         *(volatile unsigned long long*)&ctl->total_units = units;
         *(volatile unsigned long long*)&ctl->dyn_next = static_units(units);
-        *(volatile int*)&ctl->rounds += 1;   // one closing thread at a time
+        atomicAdd(&ctl->rounds, 1);           // result unused: a reduction, no round trip
         // After the caller's __syncthreads, this fence makes the block's new states and the
         // job's new frontier visible device-wide before the next round reads them via L2.
         __threadfence();
