@@ -61,32 +61,39 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
         const int j = base + threadIdx.x;
         unsigned long long units = 0;
         if (j < njobs) {
-            // The previous round may have been closed by another SM: read every field that
-            // changes during a run through L2 (volatile), never from this SM's L1.
+            // The previous round may have been closed by another SM: the fields that change
+            // during a run are read through L2 (relaxed loads, never this SM's L1), all in one
+            // round trip, and nothing is read back after a write.
             JobDev& J = jobs[j];
-            volatile JobDev& V = jobs[j];
-            if (V.status == kRunning) {
-                const unsigned long long tail = ld_relaxed_ull(&J.tail);
-                const unsigned long long hi = V.hi;
-                if (ld_relaxed_int(&J.overflow)) {
-                    V.status = kNeedMem;
+            unsigned long long lo, hi, tail, rs;
+            asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(&J.lo));
+            asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(tail), "=l"(rs) : "l"(&J.tail));
+            const int overflow = ld_relaxed_int(&J.overflow);
+            int radius = (int)(unsigned)(rs & 0xffffffffull);
+            int status = (int)(unsigned)(rs >> 32);
+            if (status == kRunning) {
+                volatile JobDev& V = jobs[j];
+                if (overflow) {
+                    status = kNeedMem;
                 } else {
                     const unsigned long long fresh = tail - hi;
                     if (fresh == 0) {
-                        V.status = kDone;
+                        status = kDone;
                     } else {
-                        const int r = V.radius + 1;
-                        J.layer_sizes[r] = fresh;
-                        V.radius = r;
+                        radius += 1;
+                        J.layer_sizes[radius] = fresh;
+                        V.radius = radius;
                         V.lo = hi;
                         V.hi = tail;
-                        if (J.max_radius >= 0 && r >= J.max_radius) V.status = kTruncRadius;
-                        else if (J.stop_above > 0 && fresh > J.stop_above) V.status = kTruncAbove;
-                        else if (r + 1 >= J.layers_cap) V.status = kTruncRadius;
+                        if (J.max_radius >= 0 && radius >= J.max_radius) status = kTruncRadius;
+                        else if (J.stop_above > 0 && fresh > J.stop_above) status = kTruncAbove;
+                        else if (radius + 1 >= J.layers_cap) status = kTruncRadius;
+                        if (status == kRunning) units = (fresh + 31) >> 5;
                     }
                 }
-                if (V.status == kRunning) units = (V.hi - V.lo + 31) >> 5;
+                if (status != kRunning) V.status = status;
             }
+            (void)lo;
         }
         // block-wide exclusive scan of units
         unsigned long long v = units;
