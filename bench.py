@@ -47,6 +47,44 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def measured_record(kernel_name, workload, settings=None):
+    """The committed ncu record of `kernel_name` on `workload` (profiles/traffic.json), or None
+    when there is none, the kernel's sources changed since it was taken, or it was taken under
+    other launch settings."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel_name)
+        if not rec or rec.get("workload") != workload:
+            return None
+        if "settings" in rec and rec["settings"] != (settings or rec["settings"]):
+            return None
+        h = hashlib.sha256()
+        for src in rec["kernel_sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec if h.hexdigest() == rec["kernel_sources_sha256"] else None
+    except Exception:
+        return None
+
+
+def issue_roofline(kernel_name, workload, kernel_ms, sm_mhz):
+    """Warp instructions issued per second against the SMs' issue rate (4 schedulers per SM, one
+    warp instruction per scheduler per clock, at the SM clock sampled during the run), from the
+    instruction count of the committed ncu record; None without a current record."""
+    rec = measured_record(kernel_name, workload)
+    if not rec or "warp_instructions" not in rec or not kernel_ms:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = sms * 4 * mhz * 1e6 / 1e12
+    achieved = rec["warp_instructions"] / (kernel_ms / 1000.0) / 1e12
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "T warp-instr/s",
+            "frac": achieved / peak, "warp_instructions": rec["warp_instructions"],
+            "peak_source": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (sampled)"}
+
+
 def measured_traffic(kernel_name, workload, settings=None):
     """DRAM bytes per launch of `kernel_name` on `workload` from the committed ncu record
     (profiles/traffic.json), or None when there is none, the kernel's sources changed since it
@@ -376,6 +414,8 @@ def run_ours(args):
                        strat_name, " (visited set; one persistent cooperative launch)"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline_issue": issue_roofline(kernel_name, job.name, kern_ms_per,
+                                         (clocks or {}).get("sm_mhz")),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": measured_traffic(kernel_name, job.name),
