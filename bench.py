@@ -573,7 +573,7 @@ def run_serve(args):
         cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=job_cap, stream=stream)
     lam1 = len(sample) / (time.perf_counter() - t0)
     lines = []
-    for mult in (1.0, 2.0):
+    for mult in (1.0, 2.0, 4.0):
         lam = lam1 * mult
         arr = [j.arrival / lam for j in jobs]
         with Server(mem_budget=budget, max_slots=args.serve_slots, job_mem_cap=job_cap,
