@@ -209,65 +209,42 @@ __device__ __forceinline__ void table_insert_multi_slot(uint64_t* table, uint64_
         if (pend >> i & 1u) res[i] = -1;
 }
 
-// Lehmer rank of the permutation packed in `key` (element i in nibble i), a bijection of S_n
-// onto [0, n!): digit c_i = number of elements after position i that are smaller than p[i],
-// i.e. p[i] minus the smaller values already used; rank = sum c_i (n-1-i)!, evaluated in
-// Horner form.
-// The same rank with n known at compile time (N > 0): the loop unrolls with constant digit
-// positions and multipliers.
+// Index of a permutation in a bitmap over S_n: the position-major Lehmer rank
+//     rank(s) = sum_{i=1}^{n-1} d_i * i!,   d_i = #{ j < i : s_j < s_i },
+// a bijection onto [0, n!) (identity -> n!-1, full reversal -> 0).  A generator that moves only
+// positions below j changes only the digits below j, so the image of a state lies within j!
+// ranks of it: the probes of prefix reversals and other short-support generators of one state
+// share cache lines.  Digits are taken from the top position down, d_i = s_i - #{j > i : s_j <
+// s_i}; the digits of positions 12.. and 1..11 form two 32-bit Horner sums, then joined.
 template <int N>
 __device__ __forceinline__ uint64_t perm_rank_n(uint64_t key) {
-    unsigned used = 0;
-    if (N <= 12) {
-        unsigned r = 0;
+    unsigned right = 0, top = 0, low = 0;
 #pragma unroll
-        for (int i = 0; i < N - 1; ++i) {
-            const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-            const unsigned c = v - __popc(used & ((1u << v) - 1u));
-            used |= 1u << v;
-            r = r * (unsigned)(N - i) + c;
-        }
-        return r;
-    }
-    uint64_t r = 0;
-#pragma unroll
-    for (int i = 0; i < N - 1; ++i) {
+    for (int i = N - 1; i >= 1; --i) {
         const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-        const unsigned c = v - __popc(used & ((1u << v) - 1u));
-        used |= 1u << v;
-        r = r * (uint64_t)(N - i) + c;
+        const unsigned d = v - __popc(right & ((1u << v) - 1u));
+        right |= 1u << v;
+        if (i >= 12) top = top * (unsigned)(i + 1) + d;
+        else low = low * (unsigned)(i + 1) + d;
     }
-    return r;
+    if (N > 12) return (uint64_t)top * 479001600ull + low;   // 12!
+    return low;
 }
 
+// The same rank with n known only at run time (n <= 16).
 __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
-    // The last digit is always 0 and is skipped; the loop is unrolled so every nibble shift is
-    // a constant.  For n <= 12 the rank fits in 32 bits.
-    unsigned used = 0;
-    if (n <= 12) {
-        unsigned r = 0;
+    unsigned right = 0, top = 0, low = 0;
 #pragma unroll
-        for (int i = 0; i < 11; ++i) {
-            if (i < n - 1) {
-                const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-                const unsigned c = v - __popc(used & ((1u << v) - 1u));
-                used |= 1u << v;
-                r = r * (unsigned)(n - i) + c;
-            }
-        }
-        return r;
-    }
-    uint64_t r = 0;
-#pragma unroll
-    for (int i = 0; i < 15; ++i) {
-        if (i < n - 1) {
+    for (int i = 15; i >= 1; --i) {
+        if (i < n) {
             const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-            const unsigned c = v - __popc(used & ((1u << v) - 1u));
-            used |= 1u << v;
-            r = r * (uint64_t)(n - i) + c;
+            const unsigned d = v - __popc(right & ((1u << v) - 1u));
+            right |= 1u << v;
+            if (i >= 12) top = top * (unsigned)(i + 1) + d;
+            else low = low * (unsigned)(i + 1) + d;
         }
     }
-    return r;
+    return (uint64_t)top * 479001600ull + low;
 }
 
 // Visited test-and-set of G keys in a rank-indexed bitmap (one bit per element of S_n): one

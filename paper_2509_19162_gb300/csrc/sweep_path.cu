@@ -42,25 +42,12 @@ __host__ __device__ constexpr uint64_t fact(int i) { return i <= 1 ? 1ull : (uin
 __host__ __device__ constexpr unsigned weight_low(int i) { return (unsigned)fact(i); }
 __host__ __device__ constexpr unsigned weight_top(int i) { return (unsigned)(fact(i) / fact(12)); }
 
-// rank(s) for a packed permutation of 0..N-1 (element i in bits 4i..4i+3), N <= 16.  Digits are
-// taken from the top position down: d_i = s_i - #{j > i : s_j < s_i}.  The digits of positions
-// 12.. and 1..11 are combined in two 32-bit Horner sums (both fit), then joined.
+// The rank of the bitmaps is perm_rank_n / perm_rank (cg_device.cuh), the position-major Lehmer
+// rank.
 template <int N>
-__device__ __forceinline__ uint64_t pos_rank(uint64_t key) {
-    unsigned right = 0, top = 0, low = 0;
-#pragma unroll
-    for (int i = N - 1; i >= 1; --i) {
-        const unsigned v = (unsigned)(key >> (4 * i)) & 15u;
-        const unsigned d = v - __popc(right & ((1u << v) - 1u));
-        right |= 1u << v;
-        if (i >= 12) top = top * (unsigned)(i + 1) + d;
-        else low = low * (unsigned)(i + 1) + d;
-    }
-    if (N > 12) return (uint64_t)top * fact(12) + low;
-    return low;
-}
+__device__ __forceinline__ uint64_t pos_rank(uint64_t key) { return perm_rank_n<N>(key); }
 
-// Inverse of pos_rank: from the top position down, position i holds the d_i-th smallest of the
+// Inverse of the rank: from the top position down, position i holds the d_i-th smallest of the
 // values not yet placed.  The unplaced values are kept sorted in the nibbles of `avail`.
 template <int N>
 __device__ __forceinline__ uint64_t pos_unrank(uint64_t r) {
