@@ -289,11 +289,10 @@ __device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns) {
         const unsigned gsize = (gridDim.x - g + kBarGroups - 1) / kBarGroups;
         const unsigned ngroups = gridDim.x < (unsigned)kBarGroups ? gridDim.x : (unsigned)kBarGroups;
         int state = 0;
-        if (atomicAdd(&ctl->group[g].count, 1u) == gsize - 1) {
-            atomicExch(&ctl->group[g].count, 0u);
-            __threadfence();
-            if (atomicAdd(&ctl->bar_count, 1u) == ngroups - 1) {
-                atomicExch(&ctl->bar_count, 0u);
+        // The counters only grow (zeroed before each launch): barrier `gen` is complete in a
+        // group when its counter reaches gsize * (gen + 1), so nothing is reset on the way.
+        if (atomicAdd(&ctl->group[g].count, 1u) == gsize * (gen + 1) - 1) {
+            if (atomicAdd(&ctl->bar_count, 1u) == ngroups * (gen + 1) - 1) {
                 __threadfence();
                 state = 1;
             }

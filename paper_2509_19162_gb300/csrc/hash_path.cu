@@ -496,6 +496,7 @@ __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* u
     ctl->rounds = 0;
     ctl->bar_count = 0;
     ctl->bar_gen = 0;
+    for (int g = 0; g < kBarGroups; ++g) ctl->group[g].count = 0;   // the barrier counters only grow
     ctl->err = 0;
 }
 
