@@ -277,18 +277,23 @@ __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words
 // the others (cooperative launch: all blocks co-resident).  Returns 1 in every thread of the
 // block that arrived last (it must call grid_release after its work), 0 in the other blocks
 // once the last block has released them, -1 on error (timeout or an error word set by
-// another block: the caller returns from the kernel).
-__device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns) {
+// another block: the caller returns from the kernel).  `word` receives the barrier word: for
+// the last block the one it arrived on (pass it to grid_release), for the others the one the
+// release wrote, whose payload is word >> kGenBits.
+__device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns, unsigned long long& word) {
     __shared__ int s_state;
+    __shared__ unsigned long long s_word;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &ctl->bar_gen;
-        const unsigned int gen = *vgen;
+        volatile unsigned long long* vword = &ctl->bar_word;
+        const unsigned long long w0 = *vword;
+        const unsigned gen = (unsigned)(w0 & kGenMask);
         __threadfence();
         const unsigned g = blockIdx.x % kBarGroups;
         const unsigned gsize = (gridDim.x - g + kBarGroups - 1) / kBarGroups;
         const unsigned ngroups = gridDim.x < (unsigned)kBarGroups ? gridDim.x : (unsigned)kBarGroups;
         int state = 0;
+        unsigned long long w = w0;
         // The counters only grow (zeroed before each launch): barrier `gen` is complete in a
         // group when its counter reaches gsize * (gen + 1), so nothing is reset on the way.
         if (atomicAdd(&ctl->group[g].count, 1u) == gsize * (gen + 1) - 1) {
@@ -300,7 +305,7 @@ __device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns) {
         if (state == 0) {
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
-            while (*vgen == gen) {
+            while (((w = *vword) & kGenMask) == gen) {
                 if ((++spins & 63u) == 0) {
                     if (*(volatile int*)&ctl->err != 0) { state = -1; break; }
                     if (globaltimer_ns() - t0 > timeout_ns) {
@@ -315,17 +320,21 @@ __device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns) {
             if (state == 0 && *(volatile int*)&ctl->err != 0) state = -1;
         }
         s_state = state;
+        s_word = w;
     }
     __syncthreads();
+    word = s_word;
     return s_state;
 }
 
-// Release half: called by every thread of the last arriving block after its work.
-__device__ __forceinline__ void grid_release(Ctl* ctl) {
+// Release half: called by every thread of the last arriving block after its work, with the
+// word grid_arrive gave it and the payload for every block (below 2^(64 - kGenBits)).
+__device__ __forceinline__ void grid_release(Ctl* ctl, unsigned long long word, unsigned long long payload) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(&ctl->bar_gen, 1u);
+        const unsigned long long gen = ((word & kGenMask) + 1) & kGenMask;
+        atomicExch(&ctl->bar_word, gen | (payload << kGenBits));
     }
 }
 

@@ -124,12 +124,17 @@ struct alignas(128) SweepDev {
 // the top counter; every counter and the generation word that waiting blocks poll sit in
 // their own 128-byte line, so neither arrivals nor polling queue at one L2 slice.
 constexpr int kBarGroups = 32;
+constexpr int kGenBits = 20;
+constexpr unsigned long long kGenMask = (1ull << kGenBits) - 1;
 
 struct alignas(128) Ctl {
     unsigned int bar_count;
     unsigned int pad0[31];
-    unsigned int bar_gen;
-    unsigned int pad1[31];
+    // Barrier word: the low kGenBits bits count the barriers completed in this launch; the rest
+    // is a payload the releasing block hands to every block (for a single job: the size of the
+    // next frontier, 0 when the growth stops).
+    unsigned long long bar_word;
+    unsigned int pad1[30];
     int err;                        // 0, or a CG_E* code set by a kernel
     int rounds;                     // rounds completed
     unsigned long long total_units; // warp work units of the current round

@@ -131,7 +131,11 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
 // close_round for a launch with one job, by one thread (no block-wide scan).  Called by every
 // thread of the closing block.
 
-__device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl) {
+// The closing block's thread 0 also receives the next frontier: *next_fresh = its size (0 when
+// the growth stops), *next_lo/*next_hi its bounds in the key array.
+__device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl,
+                                   unsigned long long* next_fresh, unsigned long long* next_lo,
+                                   unsigned long long* next_hi) {
     if (threadIdx.x == 0) {
         JobDev& J = jobs[0];
         // The round's state in one round trip: (lo, hi), (tail, radius | status << 32), overflow
@@ -172,6 +176,9 @@ __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* 
         *(volatile unsigned long long*)&ctl->total_units = units;
         *(volatile unsigned long long*)&ctl->dyn_next = static_units(units);
         atomicAdd(&ctl->rounds, 1);           // result unused: a reduction, no round trip
+        *next_fresh = units ? tail - hi : 0;
+        *next_lo = hi;
+        *next_hi = tail;
         // After the caller's __syncthreads, this fence makes the block's new states and the
         // job's new frontier visible device-wide before the next round reads them via L2.
         __threadfence();
@@ -304,9 +311,8 @@ __device__ __forceinline__ unsigned long long draw_unit(unsigned long long& coun
 template <int kProbeILP, int kMode, int kN = 0>
 __device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsigned long long& s_unit,
                                              unsigned long long ue, unsigned long long total,
-                                             unsigned long long* dyn, uint64_t* buf, int lane) {
-    const unsigned long long lo = ld_relaxed_ull(&J->lo);
-    const unsigned long long hi = ld_relaxed_ull(&J->hi);
+                                             unsigned long long* dyn, uint64_t* buf, int lane,
+                                             unsigned long long lo, unsigned long long hi) {
     int cnt = 0;
     bool overflow_seen = false;
     unsigned iter = 0;
@@ -346,6 +352,10 @@ __device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsig
     stage_flush_block(buf, cnt, J, lane);
 }
 
+// Barrier payload of a single-job round: the next frontier's size, with this bit set when the
+// releasing block ran rounds alone before releasing (the other blocks reload the bounds).
+constexpr unsigned long long kReloadFlag = 1ull << 42;
+
 // Rounds of at most this many units (one per warp of a block) are run by one block alone.
 constexpr unsigned long long kSoloUnits = kGrowBlock / 32;
 
@@ -369,9 +379,23 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
     }
     const int lane = threadIdx.x & 31;
     uint64_t* buf = s_stage[threadIdx.x >> 5];
+    // One job: every block keeps the frontier bounds itself.  They are read once here; after
+    // each barrier the releasing block hands every block the size of the next frontier in the
+    // barrier word, so no block reloads them.  (Several jobs: the round's layout is read from
+    // the control block each round.)
+    __shared__ unsigned long long s_lo, s_hi, s_total, s_fresh;
+    if (threadIdx.x == 0 && !kMulti) {
+        const bool running = ld_relaxed_int(&jobs[0].status) == kRunning;
+        s_lo = ld_relaxed_ull(&jobs[0].lo);
+        s_hi = running ? ld_relaxed_ull(&jobs[0].hi) : s_lo;
+    }
 
     for (int round = 0; round < max_rounds; ++round) {
-        const unsigned long long total = ld_relaxed_ull(&ctl->total_units);
+        if (threadIdx.x == 0)
+            s_total = kMulti ? ld_relaxed_ull(&ctl->total_units) : (s_hi - s_lo + 31) >> 5;
+        __syncthreads();
+        const unsigned long long total = s_total;
+        const unsigned long long lo = s_lo, hi = s_hi;
         if (total == 0) break;
         // Rounds of at least 16 units per block share their second half (blocks that finish
         // their range early take from it); smaller rounds are split in equal ranges only.
@@ -383,7 +407,8 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         bool overflow_seen = false;
         if (!kMulti) {
             phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, stat * (blockIdx.x + 1) / gridDim.x,
-                                               total, shared_tail ? &ctl->dyn_next : nullptr, buf, lane);
+                                               total, shared_tail ? &ctl->dyn_next : nullptr, buf, lane,
+                                               lo, hi);
         } else {
             int cur = -1;
             JobDev* J = nullptr;
@@ -430,27 +455,49 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         }
         // One barrier per round: the last block to finish the round closes it (layer counts,
         // stop tests, next round's work layout) and then releases the others.
-        const int arrive = grid_arrive(ctl, timeout_ns);
+        unsigned long long word = 0;
+        const int arrive = grid_arrive(ctl, timeout_ns, word);
         if (arrive < 0) return;
         if (arrive == 1) {
             if (!kMulti) {
-                close_round_single(jobs, ubeg, ctl);
+                close_round_single(jobs, ubeg, ctl, &s_fresh, &s_lo, &s_hi);
                 // While the frontier stays small this block runs the next rounds alone, with
                 // __syncthreads for a barrier; the other blocks wait until it releases them.
+                bool solo = false;
                 for (;;) {
-                    const unsigned long long t = *(volatile unsigned long long*)&ctl->total_units;
+                    const unsigned long long t = (s_fresh + 31) >> 5;
                     if (t == 0 || t > kSoloUnits || round + 1 >= max_rounds) break;
                     ++round;
+                    solo = true;
+                    const unsigned long long slo = s_lo, shi = s_hi;
                     if (threadIdx.x == 0) s_unit = 0;
                     __syncthreads();
-                    phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, t, t, nullptr, buf, lane);
+                    phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, t, t, nullptr, buf, lane,
+                                                       slo, shi);
                     __syncthreads();
-                    close_round_single(jobs, ubeg, ctl);
+                    close_round_single(jobs, ubeg, ctl, &s_fresh, &s_lo, &s_hi);
                 }
+                if (threadIdx.x == 0 && s_fresh == 0) s_hi = s_lo;   // stop: empty frontier
+                // payload: the next frontier's size, and whether this block ran rounds alone (the
+                // others' bounds are then stale and they reload them)
+                grid_release(ctl, word, s_fresh | (solo ? kReloadFlag : 0ull));
             } else {
                 close_round(jobs, njobs, ubeg, ctl);
+                grid_release(ctl, word, 0);
             }
-            grid_release(ctl);
+        } else if (!kMulti && threadIdx.x == 0) {
+            // the next frontier follows this one in the key array (size 0: the growth stops)
+            const unsigned long long payload = word >> kGenBits;
+            const unsigned long long fresh = payload & ~kReloadFlag;
+            if (fresh == 0) {
+                s_lo = s_hi;
+            } else if (payload & kReloadFlag) {
+                s_lo = ld_relaxed_ull(&jobs[0].lo);
+                s_hi = ld_relaxed_ull(&jobs[0].hi);
+            } else {
+                s_lo = s_hi;
+                s_hi = s_hi + fresh;
+            }
         }
     }
 }
@@ -495,7 +542,7 @@ __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* u
     ctl->dyn_next = static_units(acc);
     ctl->rounds = 0;
     ctl->bar_count = 0;
-    ctl->bar_gen = 0;
+    ctl->bar_word = 0;
     for (int g = 0; g < kBarGroups; ++g) ctl->group[g].count = 0;   // the barrier counters only grow
     ctl->err = 0;
 }

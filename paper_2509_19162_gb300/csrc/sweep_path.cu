@@ -314,11 +314,12 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
         __syncthreads();
         if (threadIdx.x == 0 && s_fresh) atomicAdd(&D.fresh, s_fresh);
 
-        const int arrive = grid_arrive(ctl, timeout_ns);
+        unsigned long long word = 0;
+        const int arrive = grid_arrive(ctl, timeout_ns, word);
         if (arrive < 0) return;
         if (arrive == 1) {
             if (threadIdx.x == 0) sweep_close(D, ctl);
-            grid_release(ctl);
+            grid_release(ctl, word, 0);
         }
     }
 }
