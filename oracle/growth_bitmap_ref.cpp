@@ -15,8 +15,11 @@
  * group instead of a list of states), so that the whole of S_14 (87,178,291,200 states) fits in
  * host memory: three bitmaps of n!/8 bytes (seen, current layer, next layer), 32.7 GB for n = 14.
  * Each layer step visits the set bits of the current layer in rank order, unranks each (the
- * factorial-base digits, each picking the c-th smallest unused value), applies every generator,
+ * factorial-base digits, each picking the d-th smallest unused value), applies every generator,
  * ranks the image and claims its bit in `seen`; a new state also sets its bit in the next layer.
+ * Its index is the position-major Lehmer rank (posmajor_rank), under which the images of a state
+ * by short-support generators lie near it, so the bit updates of neighbouring states share
+ * cache lines.
  * Pinned to oracle A and oracle B in tests/test_oracle_pins.py.
  *
  * Only tests/ and the committed golden-value script may call this code.
@@ -92,6 +95,41 @@ uint64_t lehmer_rank_mask(const uint8_t* p, int n, const uint64_t* fact) {
         r += (uint64_t)c * fact[n - 1 - i];
     }
     return r;
+}
+
+// Position-major Lehmer rank, rank(p) = sum_{i>=1} d_i i!, d_i = #{ j < i : p[j] < p[i] }: another
+// bijection S_n -> [0, n!), used by oracle C because a generator that moves only positions
+// below j changes only the digits below j, keeping its image within j! ranks (cache-friendly
+// for prefix reversals and adjacent transpositions).  Digits from the top position down: d_i is
+// p[i] minus the smaller values at positions above i.
+uint64_t posmajor_rank(const uint8_t* p, int n, const uint64_t* fact) {
+    uint64_t r = 0;
+    unsigned above = 0;
+    for (int i = n - 1; i >= 1; --i) {
+        const unsigned d = p[i] - (unsigned)__builtin_popcount(above & ((1u << p[i]) - 1u));
+        above |= 1u << p[i];
+        r += (uint64_t)d * fact[i];
+    }
+    return r;
+}
+
+// Inverse: from the top position down, position i takes the d_i-th smallest unused value.
+void posmajor_unrank(uint64_t r, int n, const uint64_t* fact, uint8_t* p) {
+    unsigned unused = (1u << n) - 1u;
+    for (int i = n - 1; i >= 1; --i) {
+        unsigned d = (unsigned)(r / fact[i]);
+        r -= (uint64_t)d * fact[i];
+        int v = 0;
+        for (;; ++v) {
+            if ((unused >> v) & 1u) {
+                if (d == 0) break;
+                --d;
+            }
+        }
+        p[i] = (uint8_t)v;
+        unused &= ~(1u << v);
+    }
+    p[0] = (uint8_t)__builtin_ctz(unused);
 }
 
 }  // namespace
@@ -235,7 +273,7 @@ int oracle_growth_bitmask(int n, int k, const uint8_t* gens, int max_radius, uin
     {
         std::vector<uint8_t> id(n);
         for (int i = 0; i < n; ++i) id[i] = (uint8_t)i;
-        const uint64_t r0 = lehmer_rank_mask(id.data(), n, fact);
+        const uint64_t r0 = posmajor_rank(id.data(), n, fact);
         seen[r0 / 64].fetch_or(1ull << (r0 % 64));
         cur[r0 / 64].fetch_or(1ull << (r0 % 64));
     }
@@ -254,10 +292,10 @@ int oracle_growth_bitmask(int n, int k, const uint8_t* gens, int max_radius, uin
                 while (bits) {
                     const int bit = __builtin_ctzll(bits);
                     bits &= bits - 1;
-                    lehmer_unrank(w * 64 + (uint64_t)bit, n, fact, s.data());
+                    posmajor_unrank(w * 64 + (uint64_t)bit, n, fact, s.data());
                     for (int j = 0; j < k; ++j) {
                         for (int i = 0; i < n; ++i) t[i] = s[gens[j * n + i]];   // t[i] = s[g[i]]
-                        const uint64_t r = lehmer_rank_mask(t.data(), n, fact);
+                        const uint64_t r = posmajor_rank(t.data(), n, fact);
                         const uint64_t m = 1ull << (r % 64);
                         if (!(seen[r / 64].fetch_or(m, std::memory_order_relaxed) & m)) {
                             nxt[r / 64].fetch_or(m, std::memory_order_relaxed);

@@ -29,6 +29,8 @@ CASES = {
     # oracle C (visited set and layers as bitmaps over all n! ranks): whole growths of S_13
     "s13_pancake_growth": (13, w.pancake(13), "bitmask", -1,
                            "S_13, 12 prefix reversals, full growth from the identity"),
+    "s14_pancake_growth": (14, w.pancake(14), "bitmask", -1,
+                           "S_14, 13 prefix reversals, full growth from the identity"),
 }
 
 
