@@ -68,11 +68,11 @@ def measured_record(kernel_name, workload, settings=None):
         return None
 
 
-def issue_roofline(kernel_name, workload, kernel_ms, sm_mhz):
+def issue_roofline(kernel_name, workload, kernel_ms, sm_mhz, settings=None):
     """Warp instructions issued per second against the SMs' issue rate (4 schedulers per SM, one
     warp instruction per scheduler per clock, at the SM clock sampled during the run), from the
     instruction count of the committed ncu record; None without a current record."""
-    rec = measured_record(kernel_name, workload)
+    rec = measured_record(kernel_name, workload, settings)
     if not rec or "warp_instructions" not in rec or not kernel_ms:
         return None
     import torch
@@ -86,24 +86,10 @@ def issue_roofline(kernel_name, workload, kernel_ms, sm_mhz):
 
 
 def measured_traffic(kernel_name, workload, settings=None):
-    """DRAM bytes per launch of `kernel_name` on `workload` from the committed ncu record
-    (profiles/traffic.json), or None when there is none, the kernel's sources changed since it
-    was taken, or it was taken under other launch settings."""
-    import hashlib
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f).get(kernel_name)
-        if not rec or rec.get("workload") != workload:
-            return None
-        if "settings" in rec and rec["settings"] != (settings or rec["settings"]):
-            return None
-        h = hashlib.sha256()
-        for src in rec["kernel_sources"]:
-            with open(os.path.join(ROOT, src), "rb") as f:
-                h.update(f.read())
-        return rec["dram_bytes"] if h.hexdigest() == rec["kernel_sources_sha256"] else None
-    except Exception:
-        return None
+    """DRAM bytes per launch of `kernel_name` on `workload` from its committed ncu record
+    (measured_record), or None without a current record."""
+    rec = measured_record(kernel_name, workload, settings)
+    return rec["dram_bytes"] if rec else None
 
 
 def algorithmic_bytes(layers, k, complete):
@@ -320,6 +306,7 @@ def run_ours(args):
     handle = cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
                        stop_above=job.stop_above, keep_last=False, strategy=args.strategy,
                        start=job.start)
+    handle.set_sweep_order(args.sweep_order)
     # warm-up (also allocates the job's buffers: inputs resident before the timed region)
     res = None
     for _ in range(args.warmup):
@@ -350,6 +337,8 @@ def run_ours(args):
     # kernel names as ncu prints them: the single-job bitmap kernel with one generator in
     # flight is compiled per n (last template argument), every other variant has 0 there
     per_n = job.n if (strat_name == "bitmap" and variant == 17 and 2 <= job.n <= 14) else 0
+    # the sweep's block order changes its memory traffic: its ncu record names the order
+    launch_settings = {"sweep_order": args.sweep_order} if strat_name == "sweep" else None
     kernel_name = {"sort": "radix sort / merge-path kernels",
                    "sweep": f"sweep_grow_kernel<{min(variant, 2)}, {job.n}>"}.get(
         strat_name, f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 0, {per_n}>")
@@ -383,6 +372,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         with cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius,
                        stop_above=job.stop_above, strategy=args.strategy, start=job.start) as g:
+            g.set_sweep_order(args.sweep_order)
             r = g.run(stream)
             st = g.stats()
         e2e_times.append(time.perf_counter() - t0)
@@ -413,12 +403,13 @@ def run_ours(args):
                                 "cooperative launch)"}.get(
                        strat_name, " (visited set; one persistent cooperative launch)"),
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   **(launch_settings or {})},
         "roofline_issue": issue_roofline(kernel_name, job.name, kern_ms_per,
-                                         (clocks or {}).get("sm_mhz")),
+                                         (clocks or {}).get("sm_mhz"), launch_settings),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": measured_traffic(kernel_name, job.name),
+                     "traffic": measured_traffic(kernel_name, job.name, launch_settings),
                      "kernel": kernel_name,
                      "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
                      "peak_source": peak_kind},
@@ -618,6 +609,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--strategy", default="auto", choices=["auto", "hash", "bitmap", "sort", "sweep"],
                     help="visited-set strategy of the single-job workloads")
+    ap.add_argument("--sweep-order", default="auto", choices=["auto", "discovery", "rank"],
+                    help="sweep strategy: order in which a round takes a layer's blocks")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batch workload: run with the library's default launch settings")
     ap.add_argument("--tune-table", default=None, help="JSON file to record tuned settings in")

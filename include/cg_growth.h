@@ -74,6 +74,12 @@ extern "C" {
                                   together, probing one slot per step; 9..12: the same with
                                   ILP = value - 8, probing a whole 32-byte sector per step;
                                   0: library chooses                                          */
+#define CG_OPT_SWEEP_ORDER  9  /* CG_STRATEGY_SWEEP: order in which a round takes the layer's
+                                  nonempty 1024-rank blocks.  0 = auto (rank order when they
+                                  fill at least a quarter of S_n and the visited bitmap, n!/8
+                                  bytes, is larger than L2; else the order of discovery);
+                                  1 = order of discovery; 2 = rank order.  The layers are the
+                                  same in every order                                          */
 /* batch options (cg_batch_set_option; CG_OPT_ILP and CG_OPT_GRID apply there too, 1..4)      */
 #define CG_OPT_BATCH_WAVE_L2 6 /* cap on the summed visited-set bytes of one launch:
                                   0 = half of L2 (default), -1 = none                          */

@@ -38,6 +38,7 @@ CG_OPT_STOP_ABOVE = 2
 CG_OPT_KEEP_LAST = 3
 CG_OPT_GRID = 4
 CG_OPT_ILP = 5
+CG_OPT_SWEEP_ORDER = 9
 
 # Every symbol include/cg_growth.h declares: name -> (restype, argtypes)
 _u8p = ctypes.POINTER(ctypes.c_uint8)

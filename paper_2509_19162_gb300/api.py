@@ -22,6 +22,7 @@ from . import _cg
 
 STRATEGIES = {"auto": _cg.CG_STRATEGY_AUTO, "hash": _cg.CG_STRATEGY_HASH, "sort": _cg.CG_STRATEGY_SORT,
               "bitmap": _cg.CG_STRATEGY_BITMAP, "sweep": _cg.CG_STRATEGY_SWEEP}
+SWEEP_ORDERS = {"auto": 0, "discovery": 1, "rank": 2}
 
 
 @dataclass
@@ -166,6 +167,16 @@ class Growth:
     def set_ilp(self, ilp: int) -> None:
         """Generators probed together per thread (1..4; 0 = library default)."""
         _cg.check(_cg.cg_growth_set_option(self._h, _cg.CG_OPT_ILP, int(ilp)), "set_ilp")
+
+    def set_sweep_order(self, order: str) -> None:
+        """Sweep strategy: the order in which a round takes a layer's nonempty blocks.
+
+        "auto" (rank order for dense layers, else order of discovery), "discovery" or "rank".
+        The layers are the same in every order."""
+        if order not in SWEEP_ORDERS:
+            raise ValueError(f"sweep order must be one of {sorted(SWEEP_ORDERS)}")
+        _cg.check(_cg.cg_growth_set_option(self._h, _cg.CG_OPT_SWEEP_ORDER, SWEEP_ORDERS[order]),
+                  "set_sweep_order")
 
     def stats(self) -> dict:
         st = _cg.cg_growth_stats()

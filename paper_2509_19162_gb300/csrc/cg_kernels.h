@@ -36,8 +36,12 @@ cudaError_t launch_hash_insert(uint64_t* table, uint64_t mask, const uint64_t* k
 // sweep strategy (sweep_path.cu)
 int sweep_max_grid(int device, int ilp, int n);
 cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st);
+// Block order of a sweep round (CG_OPT_SWEEP_ORDER): auto (rank order for layers whose nonempty
+// blocks fill at least a quarter of S_n when the visited bitmap is larger than L2, else order of
+// discovery), discovery, rank.
+constexpr int kSweepOrderAuto = 0, kSweepOrderList = 1, kSweepOrderRank = 2;
 cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
-                              int ilp, int n, cudaStream_t st);
+                              int ilp, int n, int order, cudaStream_t st);
 // Unrank the states of one layer (bitmap F, block list L[0, nlist)) into out[0, cap); *count
 // (zeroed by the caller) receives the number of states.
 cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,

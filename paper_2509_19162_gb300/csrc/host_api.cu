@@ -313,6 +313,7 @@ struct cg_growth {
     int keep_last = 0;
     int grid_override = 0;
     int ilp_override = 0;
+    int sweep_order = 0;                         // CG_OPT_SWEEP_ORDER
     int mode = -1;                               // visited set chosen at the first run
     std::vector<std::vector<uint8_t>> rows;      // the distinct non-identity generators
     int width = 4;                               // bits per element of the packed keys
@@ -652,7 +653,7 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
     }
     if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
     if ((e = cg::launch_sweep_grow(h->d_sweep, h->d_ctl, grid, cg::kMaxLayers + 1, kSweepTimeoutNs, ilp,
-                                   h->n, st)) != cudaSuccess)
+                                   h->n, h->sweep_order, st)) != cudaSuccess)
         return cuda_rc(e);
     if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
     h->stats.launches += 1;
@@ -932,6 +933,10 @@ int cg_growth_set_option(cg_growth_t h, int option, int64_t value) {
         case CG_OPT_ILP:
             if (value < 0 || value > 12 || (value > 4 && value < 9)) return CG_EINVAL;
             h->ilp_override = (int)value;
+            return CG_OK;
+        case CG_OPT_SWEEP_ORDER:
+            if (value < cg::kSweepOrderAuto || value > cg::kSweepOrderRank) return CG_EINVAL;
+            h->sweep_order = (int)value;
             return CG_OK;
         default:
             return CG_EINVAL;

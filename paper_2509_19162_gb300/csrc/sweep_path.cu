@@ -11,14 +11,15 @@
 // the block being expanded, which the L2 serves.
 //
 // One round (layer step) of the persistent cooperative kernel:
-//   work units 0 .. 32|L_r|-1: a word (32 ranks) of a nonempty 1024-rank block of layer r.  Its
-//       states are unranked, every generator applied, the images ranked and test-and-set in V
-//       (one atomicOr each); a new state sets its bit in F_{r+1}, the first bit of a block
-//       enters the block in L_{r+1} (per-warp staging, one atomic per 32 entries);
-//   work units 32|L_r| .. 32|L_r|+|L_{r-1}|-1: a block of layer r-1, cleared (F and S), so that
-//       its buffers are empty when they receive layer r+2;
+//   the blocks of layer r-1 are cleared (F and S), so that its buffers are empty when they
+//   receive layer r+2;
+//   the nonempty 1024-rank blocks of layer r are expanded: their states are unranked, every
+//   generator applied, the images ranked and test-and-set in V (one atomicOr each); a new state
+//   sets its bit in F_{r+1}, the first bit of a block enters the block in L_{r+1} (per-warp
+//   staging, one atomic per 32 entries).  Dense layers are taken in rank order (found from the
+//   per-block bits), sparse ones in the order of the block list L_r;
 //   grid barrier; the last block to arrive records |L_{r+1}| and the stop tests.
-// Units are drawn by warps from one counter in decreasing chunks (guided scheduling).
+// Warps draw the work units from one counter.
 #include <cstdio>
 #include <utility>
 
@@ -33,6 +34,8 @@ constexpr int kSweepBlock = 256;
 constexpr int kSweepWarps = kSweepBlock / 32;
 constexpr int kSweepSmemGens = 32;
 constexpr int kListStage = 64;   // staged block-list entries per warp
+constexpr unsigned long long kUnitStates = 256;  // rank order: target states per work unit
+constexpr unsigned long long kRankFill = 4;      // auto order: rank order from 1/4 of blocks
 
 __host__ __device__ constexpr uint64_t fact(int i) { return i <= 1 ? 1ull : (uint64_t)i * fact(i - 1); }
 
@@ -105,6 +108,14 @@ __device__ __forceinline__ void list_flush(unsigned* buf, int& cnt, unsigned* li
     __syncwarp();
 }
 
+// Clear block blk of a layer that is no longer needed: its 32 words and its block-bit word.
+__device__ __forceinline__ void clear_block(unsigned* F, unsigned* S, unsigned blk) {
+    uint4* pw = reinterpret_cast<uint4*>(F + (uint64_t)blk * 32);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pw[j] = make_uint4(0u, 0u, 0u, 0u);
+    S[blk >> 5] = 0u;
+}
+
 // Expand one state (lanes with `active`): apply every generator, test-and-set the images in V,
 // record the new ones in the next layer.
 template <int kILP, int kN>
@@ -168,7 +179,7 @@ __device__ void sweep_close(SweepDev& D, Ctl* ctl) {
 
 template <int kILP, int kN>
 __global__ void __launch_bounds__(kSweepBlock, 4)
-sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
+sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, int order) {
     __shared__ unsigned short s_off[kSweepWarps][1024];
     __shared__ uint64_t s_carry[kSweepWarps][32];
     __shared__ unsigned s_list[kSweepWarps][kListStage];
@@ -201,23 +212,48 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
         const unsigned* Lp = D.L[prv];
         unsigned* Ln = D.L[nxt];
         unsigned long long* ln_count = &D.lcount[nxt];
-        const unsigned long long ncur = ld_relaxed_ull(&D.lcount[cur]);
         const unsigned long long nprv = r > 0 ? ld_relaxed_ull(&D.lcount[prv]) : 0ull;
-        const unsigned long long items = ncur + nprv;
         if (threadIdx.x == 0) s_fresh = 0;
         __syncthreads();
 
-        // Work units: 32 * |L_r| words of layer r (32 ranks each), then the |L_{r-1}| blocks of
-        // layer r-1 to clear.  A warp fetches 32 units at a time (one per lane) and queues the
-        // ranks of their set bits; it expands them 32 at a time, carrying fewer than 32 over to
-        // the next fetch, so every chunk but the warp's last fills all lanes.
+        // Work units.  A warp fetches the 32 words of a 1024-rank block of layer r (one per
+        // lane), or 32 words of several blocks, and queues the ranks of their set bits; it
+        // expands them 32 at a time, carrying fewer than 32 over to the next fetch, so every
+        // chunk but the warp's last fills all lanes.  The blocks come in one of two orders:
+        //   rank order (layers whose nonempty blocks fill at least 1/kRankFill of S_n): units
+        //       are drawn one at a time from one counter; the first ceil(|L_{r-1}|/32) clear 32
+        //       blocks of layer r-1 each (F and S, one per lane); the rest cover S_n in rank
+        //       order, 2^lc blocks each, lc chosen so that a unit holds about kUnitStates
+        //       states when they are spread evenly, and the warp finds their nonempty blocks
+        //       from the block bits of layer r.  The warps of the grid then work within a
+        //       narrow range of ranks, near which the images of their states under
+        //       short-support generators fall, so those visited-set accesses hit L2;
+        //   discovery order (sparser layers, which may crowd into few ranges of S_n, and every
+        //       layer when the visited bitmap fits L2 anyway): units
+        //       are the 32 |L_r| words of the listed blocks of layer r, then the |L_{r-1}|
+        //       blocks of layer r-1 to clear, drawn in chunks of a quarter of the remaining
+        //       units' share of one warp (at least 32).
+        const unsigned long long ncur = ld_relaxed_ull(&D.lcount[cur]);
+        const bool by_rank =
+            order == kSweepOrderRank || (order == kSweepOrderAuto && ncur * kRankFill >= D.nblocks);
+        const unsigned long long fsize =
+            ld_relaxed_ull(reinterpret_cast<const unsigned long long*>(D.layer_sizes + r));
+        const unsigned long long want = fsize ? (kUnitStates * D.nblocks) / fsize : 1024ull;
+        int lc = 0;
+        while (lc < 10 && (1ull << lc) < want) ++lc;
+        const unsigned long long ncl = (nprv + 31) >> 5;
         const unsigned long long xunits = ncur * 32;
-        const unsigned long long units = xunits + nprv;
+        const unsigned long long units =
+            by_rank ? ncl + ((D.nblocks + (1ull << lc) - 1) >> lc) : xunits + nprv;
+        const unsigned* S = D.S[cur];
         unsigned fresh = 0;
         int lcnt = 0;
         unsigned ncarry = 0, T = 0, i = 0;  // queue: [0, ncarry) in carry, [ncarry, T) in off
         uint64_t lbase = 0;                 // first rank of this lane's fetched word
-        unsigned long long ua = 0, ub = 0;  // grabbed, not yet fetched units
+        bool have = false;                  // rank order: a unit's block bits are held in sw
+        unsigned sw = 0;                    //   lane l: block bits (32 blocks) of word wb + l
+        unsigned long long wb = 0;
+        unsigned long long ua = 0, ub = 0;  // discovery order: grabbed, not yet fetched units
         unsigned long long seen = 0;
         bool exhausted = false;
         const uint64_t t_round = globaltimer_ns();
@@ -254,44 +290,77 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
                 i = 0;
                 __syncwarp();
             }
-            if (ua >= ub) {
-                // guided chunk: a quarter of the remaining units' share of one warp, at least 32
-                unsigned long long a = 0, g = 0;
-                if (lane == 0) {
-                    const unsigned long long rem = seen < units ? units - seen : 0;
-                    g = rem / (4 * nwarps);
-                    if (g < 32) g = 32;
-                    a = atomicAdd(&D.grab, g);
-                }
-                a = __shfl_sync(0xffffffffu, a, 0);
-                g = __shfl_sync(0xffffffffu, g, 0);
-                if (a >= units) {
-                    exhausted = true;
-                    continue;
-                }
-                ua = a;
-                ub = a + g < units ? a + g : units;
-                seen = ub;
-            }
-            const unsigned long long u = ua + lane;
             unsigned fw = 0;
             lbase = 0;
-            if (u < ub) {
-                if (u < xunits) {
-                    const unsigned blk = __ldcg(Lc + (u >> 5));
-                    const unsigned w = (unsigned)(u & 31u);
-                    fw = __ldcg(F + (uint64_t)blk * 32 + w);
-                    lbase = ((uint64_t)blk << 10) | (w << 5);
-                } else {
-                    // clear a block of layer r-1: its 32 words and its summary word
-                    const unsigned blk = __ldcg(Lp + (u - xunits));
-                    uint4* pw = reinterpret_cast<uint4*>(P + (uint64_t)blk * 32);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) pw[j] = make_uint4(0u, 0u, 0u, 0u);
-                    SP[blk >> 5] = 0u;
+            if (by_rank) {
+                if (!have) {
+                    unsigned long long u = 0;
+                    if (lane == 0) u = atomicAdd(&D.grab, 1ull);
+                    u = __shfl_sync(0xffffffffu, u, 0);
+                    if (u >= units) {
+                        exhausted = true;
+                        continue;
+                    }
+                    if (u < ncl) {
+                        const unsigned long long e = (u << 5) + lane;
+                        if (e < nprv) clear_block(P, SP, __ldcg(Lp + e));
+                        continue;
+                    }
+                    // blocks [b0, b1) of S_n: lane l holds the bits of blocks 32 (wb + l) ..
+                    // 32 (wb + l) + 31 that fall in the range (at most 32 words: 2^lc <= 1024)
+                    const unsigned long long b0 = (u - ncl) << lc;
+                    const unsigned long long b1 =
+                        b0 + (1ull << lc) < D.nblocks ? b0 + (1ull << lc) : D.nblocks;
+                    wb = b0 >> 5;
+                    const unsigned long long w0 = (wb + lane) << 5;
+                    sw = w0 < b1 ? __ldcg(S + wb + lane) : 0u;
+                    if (lane == 0) sw &= ~((1u << (unsigned)(b0 & 31u)) - 1u);
+                    if (w0 < b1 && w0 + 32 > b1) sw &= (1u << (unsigned)(b1 - w0)) - 1u;
+                    have = true;
                 }
+                const unsigned nz = __ballot_sync(0xffffffffu, sw != 0u);
+                if (nz == 0u) {
+                    have = false;
+                    continue;
+                }
+                const int l = __ffs(nz) - 1;
+                const unsigned bits = __shfl_sync(0xffffffffu, sw, l);
+                if (lane == l) sw &= sw - 1u;
+                const unsigned long long blk = ((wb + (unsigned)l) << 5) + (unsigned)(__ffs(bits) - 1);
+                fw = __ldcg(F + blk * 32 + lane);
+                lbase = (blk << 10) | ((unsigned long long)lane << 5);
+            } else {
+                if (ua >= ub) {
+                    unsigned long long a = 0, g = 0;
+                    if (lane == 0) {
+                        const unsigned long long rem = seen < units ? units - seen : 0;
+                        g = rem / (4 * nwarps);
+                        if (g < 32) g = 32;
+                        a = atomicAdd(&D.grab, g);
+                    }
+                    a = __shfl_sync(0xffffffffu, a, 0);
+                    g = __shfl_sync(0xffffffffu, g, 0);
+                    if (a >= units) {
+                        exhausted = true;
+                        continue;
+                    }
+                    ua = a;
+                    ub = a + g < units ? a + g : units;
+                    seen = ub;
+                }
+                const unsigned long long u = ua + lane;
+                if (u < ub) {
+                    if (u < xunits) {
+                        const unsigned blk = __ldcg(Lc + (u >> 5));
+                        const unsigned w = (unsigned)(u & 31u);
+                        fw = __ldcg(F + (uint64_t)blk * 32 + w);
+                        lbase = ((uint64_t)blk << 10) | (w << 5);
+                    } else {
+                        clear_block(P, SP, __ldcg(Lp + (u - xunits)));
+                    }
+                }
+                ua = ua + 32 < ub ? ua + 32 : ub;
             }
-            ua = ua + 32 < ub ? ua + 32 : ub;
             // append the fetched ranks to the queue: offsets (lane << 5 | bit) after the carry
             const unsigned c = __popc(fw);
             unsigned incl = c;
@@ -324,7 +393,7 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
     }
 }
 
-using sweep_fn_t = void (*)(SweepDev*, Ctl*, int, uint64_t);
+using sweep_fn_t = void (*)(SweepDev*, Ctl*, int, uint64_t, int);
 
 // The sweep kernel is compiled for every n (its rank arithmetic unrolls over n) and for one or
 // two generators in flight per thread.
@@ -460,10 +529,20 @@ cudaError_t launch_sweep_init(SweepDev* d, cudaStream_t st) {
 }
 
 cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, uint64_t timeout_ns,
-                              int ilp, int n, cudaStream_t st) {
+                              int ilp, int n, int order, cudaStream_t st) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     const sweep_fn_t f = sweep_fn(ilp, n);
     if (!f) return cudaErrorInvalidValue;
+    // Rank order pays for itself through L2 hits on a visited bitmap larger than L2; when the
+    // bitmap (n!/8 bytes) fits, every layer is taken in order of discovery (S_12 Coxeter: 61 ms,
+    // against 66 ms with its dense layers in rank order).
+    if (order == kSweepOrderAuto) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess && l2 > 0 &&
+            fact(n) / 8 <= (uint64_t)l2)
+            order = kSweepOrderList;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kSweepBlock);
@@ -474,7 +553,7 @@ cudaError_t launch_sweep_grow(SweepDev* d, Ctl* ctl, int grid, int max_rounds, u
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, f, d, ctl, max_rounds, timeout_ns);
+    return cudaLaunchKernelEx(&cfg, f, d, ctl, max_rounds, timeout_ns, order);
 }
 
 cudaError_t launch_sweep_export(const unsigned* F, const unsigned* L, unsigned long long nlist, int n,

@@ -67,6 +67,10 @@ def test_create_validation(lib):
     assert rc == 0 and h.value
     assert lib.cg_growth_set_option(h, 99, 0) == lib.CG_EINVAL
     assert lib.cg_growth_set_option(h, lib.CG_OPT_STRATEGY, 7) == lib.CG_EINVAL
+    assert lib.cg_growth_set_option(h, lib.CG_OPT_SWEEP_ORDER, 3) == lib.CG_EINVAL
+    assert lib.cg_growth_set_option(h, lib.CG_OPT_SWEEP_ORDER, -1) == lib.CG_EINVAL
+    for order in (0, 1, 2):
+        assert lib.cg_growth_set_option(h, lib.CG_OPT_SWEEP_ORDER, order) == 0
     assert lib.cg_growth_destroy(h) == 0
     assert lib.cg_growth_destroy(None) == 0
     # sort strategy needs an inverse-closed set

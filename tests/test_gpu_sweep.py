@@ -72,6 +72,29 @@ def test_families_vs_oracle(cg, family, n):
     assert cg.growth(n, gens, strategy="sweep").layers == oracle.growth(n, gens)[0]
 
 
+@pytest.mark.parametrize("order", ["discovery", "rank"])
+@pytest.mark.parametrize("family,n", [("pancake", 10), ("coxeter", 10), ("lrx", 9), ("star", 10),
+                                      ("three_cycles", 8), ("reversals", 9)])
+def test_block_orders_vs_oracle(cg, family, n, order):
+    # every layer taken in one block order (auto mixes the two by layer density)
+    gens = w.FAMILIES[family](n)
+    with cg.Growth(n, gens, strategy="sweep") as g:
+        g.set_sweep_order(order)
+        assert g.run().layers == oracle.growth(n, gens)[0]
+
+
+@pytest.mark.parametrize("order", ["discovery", "rank"])
+def test_block_orders_s12_coxeter_and_start(cg, order):
+    with cg.Growth(12, w.coxeter(12), strategy="sweep") as g:
+        g.set_sweep_order(order)
+        assert g.run().layers == mahonian(12)
+    start = [3, 0, 7, 1, 6, 2, 5, 4, 8]
+    gens = w.pancake(9)
+    with cg.Growth(9, gens, strategy="sweep", start=start) as g:
+        g.set_sweep_order(order)
+        assert g.run().layers == oracle.growth(9, gens)[0]   # a coset of the whole group
+
+
 def test_s11_lrx_and_s10_lx(cg):
     assert cg.growth(11, w.lrx(11), strategy="sweep").layers == golden("s11_lrx_growth")
     assert cg.growth(10, w.lx(10), inverse_closed=False, strategy="sweep").layers == golden("s10_lx_growth")
