@@ -182,6 +182,12 @@ typedef struct cg_growth_stats {
     uint64_t table_slots;       /* visited-table slots (hash strategy) */
     int strategy_used;          /* CG_STRATEGY_HASH, _SORT or _BITMAP: what the run used */
     int probe_variant;          /* kernel variant of the run (generators probed together) */
+    int switched_to_sort;       /* 1: AUTO, inverse-closed set: the states stored by the hash or
+                                   bitmap path outgrew mem_cap at layer sort_from + 1, and the
+                                   sorted layer step (which keeps only the last two layers) took
+                                   the growth on from layer sort_from; strategy_used is then
+                                   CG_STRATEGY_SORT.  0: no switch                              */
+    int sort_from;
 } cg_growth_stats;
 int cg_growth_get_stats(cg_growth_t h, cg_growth_stats* out);
 

@@ -52,7 +52,8 @@ class cg_growth_stats(ctypes.Structure):
     _fields_ = [("kernel_ms", ctypes.c_double), ("launches", ctypes.c_int), ("rounds", ctypes.c_int),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("state_capacity", ctypes.c_uint64), ("table_slots", ctypes.c_uint64),
-                ("strategy_used", ctypes.c_int), ("probe_variant", ctypes.c_int)]
+                ("strategy_used", ctypes.c_int), ("probe_variant", ctypes.c_int),
+                ("switched_to_sort", ctypes.c_int), ("sort_from", ctypes.c_int)]
 
 
 SIGNATURES = {

@@ -463,6 +463,8 @@ void fill_static(cg_growth* h, JobDev& J) {
 }
 
 int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
+    // buffers of an earlier run that switched to the sorted step are not needed
+    if (h->d_cand || h->d_L[0]) h->release_sort(st);
     const bool fresh_alloc = (h->d_job == nullptr);
     int rc = ensure_small_buffers(h, st);
     if (rc) return rc;
@@ -723,32 +725,20 @@ int ensure_sort_buffers(cg_growth* h, uint64_t need_layer, uint64_t need_cand, u
     return CG_OK;
 }
 
-int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
-    int rc = ensure_small_buffers(h, st);
-    if (rc) return rc;
-    if (!h->d_count) {
-        h->d_count = (unsigned long long*)dev_alloc(64, st);
-        if (!h->d_count) return CG_ENOMEM;
-    }
+// Layer steps of the sort strategy from layer `radius` (d_L[cur], Fcur keys) and layer radius-1
+// (d_L[prev], Fprev keys), both sorted; sort_layers holds |L_0| .. |L_radius|.
+int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, uint64_t Fprev,
+               int radius, int* final_status) {
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
     const int bits = h->width * h->n;
-    int cur = 0, prev = 1, nxt = 2;
-    uint64_t Fcur = 1, Fprev = 0;
-    h->sort_layers.assign(1, 1);
-    rc = ensure_sort_buffers(h, 1, std::max<uint64_t>(h->k, 1), mem, st, cur, prev, 0, 0);
-    if (rc) return rc < 0 ? rc : CG_ENOMEM;
-    uint64_t id = 0;
-    for (int i = 0; i < h->n; ++i) id |= (uint64_t)i << (4 * i);
-    if (h->use_start) id = h->start_key;
-    cudaError_t e = cudaMemcpyAsync(h->d_L[cur], &id, 8, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_rc(e);
-    h->stats.h2d_bytes += 8;
+    int nxt = 3 - cur - prev;
+    int rc = CG_OK;
+    cudaError_t e = cudaSuccess;
     if (!h->ev0) {
         if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
         if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
     }
     int status = cg::kRunning;
-    int radius = 0;
     while (status == cg::kRunning) {
         if (h->max_radius >= 0 && radius >= h->max_radius) { status = cg::kTruncRadius; break; }
         const uint64_t C = (uint64_t)h->k * Fcur;
@@ -808,6 +798,95 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
     h->stats.probe_variant = 0;
     *final_status = status;
     return CG_OK;
+}
+
+int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
+    int rc = ensure_small_buffers(h, st);
+    if (rc) return rc;
+    if (!h->d_count) {
+        h->d_count = (unsigned long long*)dev_alloc(64, st);
+        if (!h->d_count) return CG_ENOMEM;
+    }
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    h->sort_layers.assign(1, 1);
+    rc = ensure_sort_buffers(h, 1, std::max<uint64_t>(h->k, 1), mem, st, 0, 1, 0, 0);
+    if (rc) return rc < 0 ? rc : CG_ENOMEM;
+    uint64_t id = 0;
+    for (int i = 0; i < h->n; ++i) id |= (uint64_t)i << (4 * i);
+    if (h->use_start) id = h->start_key;
+    cudaError_t e = cudaMemcpyAsync(h->d_L[0], &id, 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    h->stats.h2d_bytes += 8;
+    return sort_steps(h, st, 0, 1, 1, 0, 0, final_status);
+}
+
+
+// AUTO, undirected generating set: when the states stored by the visited-set path outgrow
+// mem_cap, the growth goes on with the sorted layer step, which keeps only the last two layers
+// (in an undirected graph the neighbours of layer r lie in layers r-1, r and r+1).  Layers
+// L_{r-1} and L_r are read back, stripped of their parent-edge tags and sorted; the key store
+// and the visited set are released first.  Nothing changes (the truncation stands) when the
+// sorted step's buffers for layer r would not fit mem_cap either.
+int continue_sorted(cg_growth* h, cudaStream_t st, int* final_status) {
+    const JobDev J = h->host_job;
+    const int r = J.radius;
+    if (r < 0 || J.hi < J.lo) return CG_EDEVICE;
+    const uint64_t Fcur = J.hi - J.lo;
+    std::vector<uint64_t> sizes((size_t)r + 1);
+    cudaError_t e = cudaMemcpyAsync(sizes.data(), h->d_layers, sizeof(uint64_t) * sizes.size(),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+    h->stats.d2h_bytes += sizeof(uint64_t) * sizes.size();
+    const uint64_t Fprev = r > 0 ? sizes[r - 1] : 0;
+    if (sizes[r] != Fcur || J.lo < Fprev) return CG_EDEVICE;
+    // the sorted step's first buffers, as ensure_sort_buffers sizes them at their smallest
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    const uint64_t need_layer = std::max<uint64_t>(std::max(Fcur, Fprev), 1);
+    const uint64_t need_cand = std::max<uint64_t>(std::max<uint64_t>((uint64_t)h->k * Fcur, Fprev), 1);
+    if (need_cand >= 0xFFFFFFFFull ||
+        3 * need_layer * 8 + need_cand * 8 + cg::sort_scratch_bytes(need_cand) > mem)
+        return CG_OK;
+    std::vector<uint64_t> keys(Fprev + Fcur);
+    if (!keys.empty()) {
+        e = cudaMemcpyAsync(keys.data(), h->d_keys + (J.lo - Fprev), keys.size() * 8,
+                            cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.d2h_bytes += keys.size() * 8;
+    }
+    if (h->n * h->width <= 60)
+        for (auto& x : keys) x &= cg::kKeyBits60;
+    dev_free(h->d_keys, st);
+    dev_free(h->d_table, st);
+    h->d_keys = nullptr;
+    h->d_table = nullptr;
+    h->keys_cap = h->table_slots = 0;
+    h->last_layer_ptr = nullptr;
+    h->last_layer_n = 0;
+    if (!h->d_count) {
+        h->d_count = (unsigned long long*)dev_alloc(64, st);
+        if (!h->d_count) return CG_ENOMEM;
+    }
+    const int cur = 0, prev = 1;
+    int rc = ensure_sort_buffers(h, need_layer, need_cand, mem, st, cur, prev, 0, 0);
+    if (rc) return rc < 0 ? rc : CG_ENOMEM;
+    if (Fprev) {
+        if ((e = cudaMemcpyAsync(h->d_L[prev], keys.data(), Fprev * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+    }
+    if ((e = cudaMemcpyAsync(h->d_L[cur], keys.data() + Fprev, Fcur * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    h->stats.h2d_bytes += keys.size() * 8;
+    const cg::SortScratch sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
+    const int bits = h->width * h->n;
+    if ((e = cg::launch_radix_sort(h->d_L[prev], Fprev, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cg::launch_radix_sort(h->d_L[cur], Fcur, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+    h->stats.launches += 2 * 3 * ((bits + 7) / 8);
+    h->sort_layers.assign(sizes.begin(), sizes.end());
+    h->stats.switched_to_sort = 1;
+    h->stats.sort_from = r;
+    return sort_steps(h, st, cur, prev, Fcur, Fprev, r, final_status);
 }
 
 }  // namespace
@@ -968,11 +1047,16 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
     int rc = use_sort ? run_sort(h, st, &status)
                       : use_sweep ? run_sweep(h, st, &status) : run_hash(h, st, &status);
     if (rc) return rc;
+    if (!use_sort && !use_sweep && status == cg::kNeedMem && h->strategy == CG_STRATEGY_AUTO &&
+        h->inverse_closed) {
+        if ((rc = continue_sorted(h, st, &status))) return rc;
+    }
+    const bool sorted = use_sort || h->stats.switched_to_sort;
     h->last_is_sweep = use_sweep;
     const int layers = h->host_job.radius + 1;
     *num_layers_out = layers;
     if (cap < layers) return CG_EINVAL;
-    if (use_sort) {
+    if (sorted) {
         for (int r = 0; r < layers; ++r) layer_sizes_out[r] = h->sort_layers[r];
     } else {
         e = cudaMemcpyAsync(layer_sizes_out, h->d_layers, sizeof(uint64_t) * layers,
