@@ -180,7 +180,7 @@ typedef struct cg_growth_stats {
     uint64_t d2h_bytes;
     uint64_t state_capacity;    /* states the job's buffers hold */
     uint64_t table_slots;       /* visited-table slots (hash strategy) */
-    int strategy_used;          /* CG_STRATEGY_HASH, _SORT or _BITMAP: what the run used */
+    int strategy_used;          /* CG_STRATEGY_HASH, _SORT, _BITMAP or _SWEEP: what the run used */
     int probe_variant;          /* kernel variant of the run (generators probed together) */
     int switched_to_sort;       /* 1: AUTO, inverse-closed set: the states stored by the hash or
                                    bitmap path outgrew mem_cap at layer sort_from + 1, and the
