@@ -92,6 +92,16 @@ def measured_traffic(kernel_name, workload, settings=None):
     return rec["dram_bytes"] if rec else None
 
 
+def with_dram_rate(roof):
+    """Add the DRAM rate the committed ncu traffic implies at the kernel time measured here
+    (traffic_gbs, and traffic_frac of the same peak) to a roofline record that has both."""
+    t, ms = roof.get("traffic"), roof.get("kernel_ms")
+    if t and ms:
+        roof["traffic_gbs"] = t / (ms / 1e3) / 1e9
+        roof["traffic_frac"] = roof["traffic_gbs"] / roof["peak"]
+    return roof
+
+
 def algorithmic_bytes(layers, k, complete):
     """Bytes the layer steps must move (per-step model B_r): read the frontier (8 F_r), write and
     read back each candidate key (16 k F_r), read layers r and r-1 for the set difference
@@ -407,12 +417,13 @@ def run_ours(args):
                    **(launch_settings or {})},
         "roofline_issue": issue_roofline(kernel_name, job.name, kern_ms_per,
                                          (clocks or {}).get("sm_mhz"), launch_settings),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": measured_traffic(kernel_name, job.name, launch_settings),
-                     "kernel": kernel_name,
-                     "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
-                     "peak_source": peak_kind},
+        "roofline": with_dram_rate({
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": measured_traffic(kernel_name, job.name, launch_settings),
+            "kernel": kernel_name,
+            "kernel_ms": kern_ms_per, "algorithmic_bytes": bytes_step,
+            "peak_source": peak_kind}),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "paper_2509_19162_gb300.Growth(...).run()"},
         "gpu_launches": launches,
@@ -525,14 +536,15 @@ def run_batch(args):
                        "tuning_s": tuned["tuning_s"]},
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "groups sharded over ranks" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0>",
-                                                 f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}",
-                                                 tuned["settings"] if tuned else None),
-                     "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0> (multi-job, "
-                               f"{launches // (3 * args.steps)} launches per batch run)",
-                     "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind},
+        "roofline": with_dram_rate({
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0>",
+                                        f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}",
+                                        tuned["settings"] if tuned else None),
+            "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0> (multi-job, "
+                      f"{launches // (3 * args.steps)} launches per batch run)",
+            "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind}),
         "e2e": {"value": nb_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": est["h2d_bytes"],
                 "d2h_bytes_per_step": est["d2h_bytes"], "api": "paper_2509_19162_gb300.Batch(...).run()"},
         "gpu_launches": launches, "clocks": clocks,

@@ -59,6 +59,12 @@ def test_ncu_records_are_gated():
     assert bench.measured_record("no_such_kernel<1>", "S11-LRX-k3-full") is None
 
 
+def test_dram_rate_from_the_ncu_traffic():
+    roof = bench.with_dram_rate({"traffic": 270_000_000, "kernel_ms": 1.5, "peak": 6750.0})
+    assert abs(roof["traffic_gbs"] - 180.0) < 1e-9 and abs(roof["traffic_frac"] - 180.0 / 6750.0) < 1e-12
+    assert "traffic_gbs" not in bench.with_dram_rate({"traffic": None, "kernel_ms": 1.5, "peak": 1.0})
+
+
 def test_sample_radius_bounds_the_oracle():
     assert bench.sample_radius(bench.get_workload("s8_coxeter"), 10.0) == -1   # whole growth fits
     r = bench.sample_radius(bench.get_workload("pancake:12"), 1.0)
