@@ -39,6 +39,8 @@ CG_OPT_KEEP_LAST = 3
 CG_OPT_GRID = 4
 CG_OPT_ILP = 5
 CG_OPT_SWEEP_ORDER = 9
+CG_NOALLOC_MAX_STATES = 1 << 20
+CG_NOALLOC_MAX_GENS = 256
 
 # Every symbol include/cg_growth.h declares: name -> (restype, argtypes)
 _u8p = ctypes.POINTER(ctypes.c_uint8)

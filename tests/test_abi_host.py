@@ -45,6 +45,30 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), f"binding lacks {name}"
 
 
+def test_header_constants_match_the_binding(lib):
+    # every #define CG_* value of the header, under the same name in the binding
+    found = 0
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"^#define\s+(CG_[A-Z0-9_]+)\s+(-?\d+\b|\(1u << \d+\))", open(h).read(),
+                             flags=re.M):
+            name, text = m.group(1), m.group(2)
+            value = 1 << int(text[7:-1]) if text.startswith("(1u") else int(text)
+            assert getattr(lib, name, None) == value, f"{name} = {value} in the header"
+            found += 1
+    assert found >= 20
+
+
+def test_stats_struct_matches_the_binding(lib):
+    # field order and types of cg_growth_stats, as declared, against the ctypes mirror
+    text = open(os.path.join(ROOT, "include", "cg_growth.h")).read()
+    body = re.search(r"typedef struct cg_growth_stats \{(.*?)\} cg_growth_stats;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    ctype = {"double": ctypes.c_double, "int": ctypes.c_int, "uint64_t": ctypes.c_uint64}
+    declared = [(m.group(2), ctype[m.group(1)])
+                for m in re.finditer(r"\b(double|int|uint64_t)\s+(\w+)\s*;", body)]
+    assert declared == list(lib.cg_growth_stats._fields_)
+
+
 def test_strerror_names_every_code(lib):
     for code in (0, 1, 2, 3, -1, -2, -3, -4, -5, -6, -7):
         assert lib.strerror(code) != "unknown code"
