@@ -58,6 +58,20 @@ def test_header_constants_match_the_binding(lib):
     assert found >= 20
 
 
+def test_prototype_arity_matches_the_binding(lib):
+    # each entry point's argument count, as declared, against the ctypes argtypes
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "cg_growth.h")).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(?:int|const char\*|uint64_t|size_t|void)\s+\**(cg_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                         text):
+        args = m.group(2).strip()
+        protos[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    assert len(protos) >= 30
+    for name, nargs in protos.items():
+        assert name in lib.SIGNATURES, name
+        assert len(lib.SIGNATURES[name][1]) == nargs, name
+
+
 def test_stats_struct_matches_the_binding(lib):
     # field order and types of cg_growth_stats, as declared, against the ctypes mirror
     text = open(os.path.join(ROOT, "include", "cg_growth.h")).read()
