@@ -6,7 +6,8 @@
 // (Section 3.4: undirected graphs are those with inverse-closed generators).  Layers are kept
 // as arrays of packed keys sorted ascending.  Per layer step:
 //   expand        candidates = every generator applied to every state of L_r
-//   radix sort    LSD, 8-bit digits over the 4n significant key bits; per pass: per-tile digit
+//   radix sort    LSD, 8-bit digits over the w n significant key bits (w = 4 bits per element
+//                 for permutations, 1 or 2 for narrow coset vectors); per pass: per-tile digit
 //                 histograms, one device-wide scan (decoupled look-back), stable scatter with
 //                 warp match_any ranking
 //   unique + diff one merge-path kernel per previous layer flags the candidates that are the
