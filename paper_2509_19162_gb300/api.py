@@ -100,8 +100,13 @@ class Growth:
     def __init__(self, n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool] = None,
                  max_radius: int = -1, mem_cap: int = 0, strategy: str = "auto",
                  stop_above: int = 0, keep_last: bool = False, start: Optional[Sequence[int]] = None):
-        """start: a central state (n values in 0..15, repeats allowed) to grow the orbit of,
-        i.e. a Schreier coset graph; None grows the Cayley graph from the identity."""
+        """n, gens: one-line permutations of 0..n-1 (t[i] = s[g[i]]).  inverse_closed: None
+        detects it.  max_radius < 0: no limit.  mem_cap: bytes every device buffer of the job
+        fits in (0: the library default); an undirected growth whose stored states outgrow it
+        goes on with the sorted two-layer step.  strategy: one of STRATEGIES.  stop_above > 0:
+        stop after the first layer with more states.  keep_last: keep the last layer for
+        last_layer().  start: a central state (n values in 0..15, repeats allowed) to grow the
+        orbit of, i.e. a Schreier coset graph; None grows the Cayley graph from the identity."""
         g = _gens_bytes(n, gens)
         if inverse_closed is None:
             inverse_closed = _is_inverse_closed(gens)
