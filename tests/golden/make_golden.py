@@ -31,10 +31,59 @@ CASES = {
                            "S_13, 12 prefix reversals, full growth from the identity"),
     "s14_pancake_growth": (14, w.pancake(14), "bitmask", -1,
                            "S_14, 13 prefix reversals, full growth from the identity"),
+    # whole S_12 growths by both large-n oracles: B (classic Lehmer rank, list frontier) and C
+    # (position-major rank, layer bitmaps) share no indexing or traversal design, so equal
+    # vectors pin C beyond the n <= 10 sizes where oracle A checks it
+    "s12_pancake_growth_b": (12, w.pancake(12), "bitmap", -1,
+                             "S_12, 11 prefix reversals, full growth from the identity"),
+    "s12_pancake_growth_c": (12, w.pancake(12), "bitmask", -1,
+                             "S_12, 11 prefix reversals, full growth from the identity"),
+    "s12_lrx_growth_b": (12, w.lrx(12), "bitmap", -1,
+                         "S_12, LRX generators, full growth from the identity"),
+    "s12_lrx_growth_c": (12, w.lrx(12), "bitmask", -1,
+                         "S_12, LRX generators, full growth from the identity"),
 }
 
 
+_BATCH = None
+
+
+def _batch_one(i):
+    j = _BATCH[i]
+    g, rc = oracle.growth(j.n, j.gens)     # full visited set: the definition, any generator set
+    assert rc == 0
+    return g
+
+
+def write_batch(name, workers=0):
+    """Config 4: the growth vector of every one of the 4096 seeded groups (oracle A, full visited
+    mode), one line per group, computed by a pool of host processes."""
+    import multiprocessing as mp
+    global _BATCH
+    jobs = w.batch_groups()
+    _BATCH = jobs
+    t0 = time.time()
+    ctx = mp.get_context("fork")             # no GPU in this process: fork is safe here
+    with ctx.Pool(workers or os.cpu_count()) as pool:
+        res = pool.map(_batch_one, range(len(jobs)), chunksize=4)
+    dt = time.time() - t0
+    path = os.path.join(HERE, name + ".txt")
+    with open(path, "w") as f:
+        f.write(f"# config 4: growth of each of the {len(jobs)} groups of workloads.batch_groups() "
+                f"(seed {w.BATCH_SEED}), in index order\n")
+        f.write(f"# written by tests/golden/make_golden.py from the CPU oracle (full visited mode, "
+                f"{dt:.0f} s on {workers or os.cpu_count()} processes); line: index n k layer_0 layer_1 ...\n")
+        for i, (j, g) in enumerate(zip(jobs, res)):
+            f.write(f"{i} {j.n} {j.k} " + " ".join(str(c) for c in g) + "\n")
+    print(name, len(res), sum(sum(g) for g in res), f"{dt:.1f}s")
+
+
+BATCH_CASES = {"batch4096_growth": write_batch}
+
+
 def write(name):
+    if name in BATCH_CASES:
+        return BATCH_CASES[name](name)
     n, gens, two, maxr, desc = CASES[name]
     t0 = time.time()
     if two == "bitmap":
@@ -58,5 +107,5 @@ def write(name):
 
 
 if __name__ == "__main__":
-    for name in (sys.argv[1:] or list(CASES)):
+    for name in (sys.argv[1:] or list(CASES) + list(BATCH_CASES)):
         write(name)

@@ -334,3 +334,40 @@ def test_oracle_c_limits_closed_forms_and_progress():
     oracle.growth_bitmask(7, w.pancake(7), progress=lambda r, s: seen.append((r, s)))
     assert [s for _, s in seen] == oracle.growth(7, w.pancake(7))[0][1:]
     assert oracle.growth_bitmask(10, w.lrx(10), max_radius=12) == oracle.growth_bitmap(10, w.lrx(10), max_radius=12)
+
+
+# ---- oracle C against oracle B on whole growths of S_12 ----
+# Oracle B indexes S_n by the classic Lehmer rank and expands a list frontier; oracle C indexes
+# it by the position-major rank and keeps every layer as a bitmap.  A mistake shared by the two
+# designs would have to appear in two different rank functions and two different traversals.
+
+def _stored(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name + ".txt")
+    return [int(l.split()[1]) for l in open(path) if not l.startswith("#")]
+
+
+@pytest.mark.parametrize("family,diameter", [("pancake", None), ("lrx", 66)])
+def test_stored_whole_s12_growths_of_oracles_b_and_c_agree(family, diameter):
+    b = _stored(f"s12_{family}_growth_b")
+    c = _stored(f"s12_{family}_growth_c")
+    assert b == c
+    assert sum(b) == math.factorial(12)
+    k = len(w.FAMILIES[family](12))
+    assert b[1] == k
+    if diameter is not None:                  # LRX: n(n-1)/2 (Section 3.3 table)
+        assert len(b) - 1 == diameter
+    else:                                     # pancake: girth 6, so sphere 2 is k(k-1)
+        assert b[2] == k * (k - 1)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not __import__("os").environ.get("CG_SLOW_TESTS"),
+                    reason="about 6 minutes on 8 host threads; set CG_SLOW_TESTS=1")
+@pytest.mark.parametrize("family", ["pancake", "lrx"])
+def test_whole_s12_growth_oracle_b_equals_oracle_c(family):
+    gens = w.FAMILIES[family](12)
+    b = oracle.growth_bitmap(12, gens)
+    c = oracle.growth_bitmask(12, gens)
+    assert b == c and b[1] == 0
+    assert b[0] == _stored(f"s12_{family}_growth_b")
