@@ -71,3 +71,70 @@ def test_late_arrivals_join_running_jobs(cg):
         assert seen_both
         assert done[b].layers == oracle.growth(8, w.coxeter(8))[0]
         assert sum(done[a].layers) == 39916800 and done[a].status == 0
+
+
+def _mahonian(n):
+    poly = np.array([1], dtype=object)
+    for j in range(1, n + 1):
+        poly = np.convolve(poly, np.ones(j, dtype=object))
+    return [int(x) for x in poly]
+
+
+def _stirling_growth(n):
+    c = [[0] * (n + 1) for _ in range(n + 1)]
+    c[0][0] = 1
+    for m in range(1, n + 1):
+        for j in range(1, m + 1):
+            c[m][j] = c[m - 1][j - 1] + (m - 1) * c[m - 1][j]
+    return [c[n][n - r] for r in range(n)]
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name + ".txt")
+    return [int(l.split()[1]) for l in open(path) if not l.startswith("#") and l.strip()]
+
+
+def test_serving_stream_full_n_range_against_closed_forms(cg):
+    # Config 5's own recipe (n = 8..16, five families, radius caps up to the family's diameter
+    # bound), first 240 jobs of the seeded stream, all arriving at once.  Every job's layers are
+    # exact: Coxeter jobs are Mahonian prefixes, all-transpositions jobs Stirling prefixes, jobs
+    # with n <= 10 the oracle's growth to the same radius, S_11..S_13 LRX / pancake jobs prefixes
+    # of the stored oracle growths; a job stopped by memory reports an exact prefix.
+    from paper_2509_19162_gb300.serve import Server, serve_stream
+    jobs = w.serve_stream(count=240)
+    assert {j.n for j in jobs} >= set(range(11, 17))
+    with Server(mem_budget=96 << 30, max_slots=256, job_mem_cap=256 << 20, rounds_per_step=4) as s:
+        rep = serve_stream(jobs, [0.0] * len(jobs), s, realtime=False)
+    stored = {("lrx", 11): _golden("s11_lrx_growth"), ("lrx", 12): _golden("s12_lrx_growth_b"),
+              ("pancake", 12): _golden("s12_pancake_growth_b"),
+              ("pancake", 13): _golden("s13_pancake_growth")}
+    checked_closed = 0
+    for j, r in zip(jobs, rep.results):
+        assert r.status in (0, 1, 2), j.name
+        if r.status == 1:
+            assert len(r.layers) == j.max_radius + 1, j.name
+        want = None
+        if j.family == "coxeter":
+            want = _mahonian(j.n)
+        elif j.family == "all_transpositions":
+            want = _stirling_growth(j.n)
+        elif (j.family, j.n) in stored:
+            want = stored[(j.family, j.n)]
+        if want is not None:
+            checked_closed += j.n >= 11
+            if r.status == 0:
+                assert r.layers == want, j.name
+            else:
+                assert r.layers == want[:len(r.layers)], j.name
+        elif j.n <= 10:
+            full, rc = oracle.growth(j.n, j.gens, max_radius=j.max_radius)
+            assert r.layers == full[:len(r.layers)], j.name
+            if r.status != 2:
+                assert r.layers == full, j.name
+        else:                                       # no closed form: the same job alone
+            alone = cg.growth(j.n, j.gens, j.inverse_closed, max_radius=j.max_radius,
+                              mem_cap=256 << 20)
+            m = min(len(alone.layers), len(r.layers))
+            assert r.layers[:m] == alone.layers[:m], j.name
+    assert checked_closed >= 40

@@ -233,3 +233,13 @@ def test_whole_s13_pancake_vs_oracle_c(cg, strategy):
     r = cg.growth(13, w.pancake(13), strategy=strategy)
     assert r.status == 0
     assert r.layers == golden("s13_pancake_growth")
+
+
+@pytest.mark.parametrize("family", ["pancake", "lrx"])
+@pytest.mark.parametrize("strategy", ["sweep", "bitmap", "hash"])
+def test_whole_s12_vs_oracle_b(cg, family, strategy):
+    # all 12! states against the classic-Lehmer-rank CPU oracle (oracle B), whose whole S_12
+    # growths also equal oracle C's (tests/golden/s12_*_growth_b.txt, _c.txt)
+    r = cg.growth(12, w.FAMILIES[family](12), strategy=strategy)
+    assert r.status == 0
+    assert r.layers == golden(f"s12_{family}_growth_b")
