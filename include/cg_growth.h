@@ -86,9 +86,12 @@ extern "C" {
 #define CG_OPT_BATCH_VISITED 7 /* CG_STRATEGY_AUTO (rank bitmap for dense groups of n <= 12),
                                   CG_STRATEGY_HASH (hash tables only) or CG_STRATEGY_BITMAP
                                   (rank bitmap whenever n <= 12 and it fits)                   */
-#define CG_OPT_GRAPH         8 /* 1: when the batch's buffers stay allocated between runs,
-                                  capture a whole run as a CUDA graph at its first run and
-                                  replay it afterwards                                         */
+#define CG_OPT_GRAPH         8 /* 1 (default): when the batch's buffers stay allocated
+                                  between runs, capture a whole run as a CUDA graph at its
+                                  first run and replay it afterwards; 0: plain launches       */
+#define CG_OPT_BATCH_ACTIVE 10 /* most jobs a batch launch grows at once (0 = min(jobs, 2048)) */
+#define CG_OPT_UNIT         11 /* batch: frontier states per warp work unit, 32 x {1, 2, 4, 8}
+                                  (4 = default)                                                */
 
 /* ---- device memory ------------------------------------------------------------------ */
 /*
@@ -106,8 +109,14 @@ int cg_set_allocator(cg_alloc_fn alloc, cg_free_fn free_fn, void* ctx);
 typedef struct cg_growth* cg_growth_t;
 
 /*
- * Create a growth job for the subgroup generated by gens.
- *   n, k            permutation length (1..16) and number of generators (>= 1).
+ * Create a growth job for the subgroup generated by gens (Section 2.1, Def. "Growth": the job's
+ * result is the sphere sizes of the Cayley graph of <gens> around the identity, or around a
+ * start vector, cg_growth_set_start).
+ *   n, k            permutation length (1..128) and number of generators (>= 1).  From the
+ *                   identity n <= 16 packs 4 bits per element in one 64-bit key and
+ *                   17 <= n <= 25 packs 5 bits per element in two words (CG_EINVAL at run
+ *                   beyond, or when a generator has more than 32 distinct offsets i - g[i]);
+ *                   longer vectors grow only from a start vector.
  *   gens            host pointer, k*n bytes, row-major: gens[j*n + i] = image of i under
  *                   generator j.  Copied; the caller keeps ownership.  Identity rows are
  *                   ignored, duplicate rows are allowed.
@@ -128,10 +137,15 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
  * given by a vector whose stabiliser is the subgroup; its growth is that of the vector's orbit,
  * Section 5.2).  start: host pointer, n values in 0..15, repeats allowed; copied.  NULL restores
  * the identity.  States are packed with the narrowest element width w of 1, 2, 4 bits that
- * holds the values (4 for a permutation), so n * w <= 64: binary vectors up to n = 64 (the
- * handle is created with n up to 64; a growth from the identity needs n <= 16).  A start with repeated values needs the HASH or SORT strategy (AUTO picks HASH;
- * BITMAP then fails at run with CG_EINVAL).  Releases buffers sized for an earlier start.
- * Errors: CG_EINVAL.
+ * holds the values (4 for a permutation of n <= 16), in one 64-bit key when n * w <= 64 and
+ * every generator has a one-word form, else in two words (n * w <= 128: 4-bit vectors up to
+ * n = 32, 2-bit up to 64, binary up to 128; CG_EINVAL beyond).  Two-word keys run the hash
+ * strategy only (AUTO or HASH; others fail at run with CG_EINVAL).  A start with repeated values
+ * needs the HASH or SORT strategy (AUTO picks HASH; BITMAP then fails at run with CG_EINVAL).
+ * A start whose values are all equal is fixed by every generator: its growth is {1}.  Releases
+ * buffers sized for an earlier start.  Errors: CG_EINVAL (also a generator that fits neither
+ * the shift-and-mask form, at most 16 distinct offsets in one word or 32 in two, nor the
+ * reversal of one contiguous range).
  */
 int cg_growth_set_start(cg_growth_t h, const uint8_t* start);
 
@@ -146,7 +160,9 @@ int cg_growth_set_option(cg_growth_t h, int option, int64_t value);
  * Returns CG_OK (growth ended: the last layer is the farthest), CG_TRUNC_* (stopped early;
  * every reported layer is exact), or an error.  If cap is too small the call returns
  * CG_EINVAL and writes the number of layers it needs to *num_layers_out.
- * A handle may be run again; each run starts from the identity.
+ * A handle may be run again; each run starts from the identity (or the start vector).
+ * The layer step (Sections 3.1.2-3.1.3): every generator applied to every state of layer r,
+ * candidates deduplicated and stripped of visited states; the strategy picks the data layout.
  */
 int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, int cap,
                   int* num_layers_out);
@@ -158,11 +174,18 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
  */
 int cg_growth_key_width(cg_growth_t h);
 
+/* 64-bit words per packed key: 1, or 2 for keys of more than 64 bits (see cg_growth_set_start
+ * and the identity of n > 16); 0 for a NULL handle. */
+int cg_growth_key_words(cg_growth_t h);
+
 /*
  * Copy the packed keys of the last reported layer (the antipodes when the growth ended) to
  * host memory keys_out (room for cap keys), in no particular order, element i of a state in
- * bits [w i, w i + w) with w = cg_growth_key_width(h); *count_out receives the layer size.  Needs CG_OPT_KEEP_LAST = 1 before the run.  Errors: CG_EINVAL (cap too small:
- * *count_out still written), CG_ECUDA.
+ * bits [w i, w i + w) with w = cg_growth_key_width(h); *count_out receives the layer size.
+ * Two-word keys (cg_growth_key_words = 2) take two entries a state, low word first, and cap
+ * then counts states (keys_out holds 2 cap words).  Needs CG_OPT_KEEP_LAST = 1 before the run
+ * (two-word keys are always kept).  Errors: CG_EINVAL (cap too small: *count_out still
+ * written), CG_ECUDA.
  */
 int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64_t* count_out);
 
@@ -263,13 +286,15 @@ int cg_batch_destroy(cg_batch_t b);
  * device slots, first come first served, while the sum of their predicted device memory stays
  * within mem_budget.  The prediction bounds the states a job can reach by its radius cap
  * (sphere r of an out-degree-k graph holds at most k (k-1)^(r-1) states when the set is
- * inverse-closed, k^r otherwise, and never more than the group order), capped at job_mem_cap
- * bytes per job (a job that needs more stops with CG_TRUNC_MEMCAP; its reported layers are
- * exact).  Each cg_server_step admits what fits, then runs up to rounds_per_step layer steps of
+ * inverse-closed, k^r otherwise, and never more than the group order), stored with the cheaper
+ * visited set (hash table, or the rank bitmap for n <= 14), capped at job_mem_cap bytes per job,
+ * the job's share of the budget (a job that needs more stops with CG_TRUNC_MEMCAP; its reported
+ * layers are exact).  Each cg_server_step admits what fits, then runs up to rounds_per_step layer steps of
  * every admitted job in one persistent launch on the caller's stream (jobs' states stay on the
  * device between steps), waits for it, and retires the jobs that ended, releasing their slot
  * and memory.  Results are the same as cg_growth_run's for the same job with the same memory.
- *   cg_server_create   mem_budget 0 = 160 GiB; job_mem_cap 0 = 2 GiB.  Errors: CG_EINVAL.
+ *   cg_server_create   mem_budget 0 = 160 GiB; job_mem_cap 0 = mem_budget / 64 (at least 1 MiB),
+ *                      so that at least 64 jobs of any size can run together.  Errors: CG_EINVAL.
  *   cg_server_submit   arguments as cg_growth_create; *job_id_out receives the job's id.
  *                      Errors: CG_EINVAL (also more than 128 distinct generators), CG_ENOTCLOSED.
  *   cg_server_step     *active_out: jobs admitted after the step; *finished_out: jobs that
@@ -279,12 +304,21 @@ int cg_batch_destroy(cg_batch_t b);
  *                      forgets it; CG_EINVAL with *num_layers_out = -1 if it has not ended, or
  *                      with the needed size if cap is too small.
  *   cg_server_load     jobs queued, jobs admitted, device bytes admitted jobs hold.
+ *   cg_server_predict  host only (no GPU work, no server needed): the admission plan of a job
+ *                      under the per-job share job_mem_cap (> 0): *states_out the predicted
+ *                      states up to its radius cap, *granted_out the states it may store (less
+ *                      than the prediction: the job may stop with CG_TRUNC_MEMCAP), *bytes_out
+ *                      the device bytes it is admitted with.  Any output may be NULL.
+ *                      Errors: CG_EINVAL, CG_ENOTCLOSED.
  */
 typedef struct cg_server* cg_server_t;
 int cg_server_create(uint64_t mem_budget, int max_slots, uint64_t job_mem_cap, int rounds_per_step,
                      cg_server_t* out);
 int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inverse_closed,
                      int max_radius, uint64_t* job_id_out);
+int cg_server_predict(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
+                      uint64_t job_mem_cap, uint64_t* states_out, uint64_t* granted_out,
+                      uint64_t* bytes_out);
 int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finished_out);
 int cg_server_finished(cg_server_t s, uint64_t* ids_out, int cap, int* count_out);
 int cg_server_result(cg_server_t s, uint64_t job_id, uint64_t* layers_out, int cap,
@@ -307,11 +341,14 @@ int cg_server_destroy(cg_server_t s);
  *   n, k, gens, inverse_closed, max_radius   as for cg_growth_create (gens: host pointer).
  *   cuda_stream                              stream to run on; synchronised before returning.
  *   layer_sizes_out, cap, num_layers_out     as for cg_growth_run (host pointers).
- * Limits: at most CG_NOALLOC_MAX_GENS generators, and the growth may visit at most
+ * Limits: at most CG_NOALLOC_MAX_GENS distinct non-identity generators (identity rows and
+ * repeated rows are dropped first, as cg_growth_create does), and the growth may visit at most
  * CG_NOALLOC_MAX_STATES states (for a complete growth: the group order); beyond either the
  * call returns CG_ETOOBIG and reports nothing.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture on that device.
+ * and caches it; make that first call before any stream capture on that device.  The cached
+ * address does not survive cudaDeviceReset: do not call this entry point on a device after
+ * resetting it in the same process.
  * All calls share the array, which keeps the last call's contents; each call clears what
  * must start empty.  Calls are serialised on the host and wait for their stream, so they do
  * not overlap; anything else that touched the array while a call runs would race with it.
@@ -322,6 +359,29 @@ int cg_server_destroy(cg_server_t s);
 int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
                           void* cuda_stream, uint64_t* layer_sizes_out, int cap,
                           int* num_layers_out);
+
+/* ---- sharded layer step (one graph over P ranks, one exchange per layer) ------------------ */
+/*
+ * The BFS layer step (Sections 3.1.2-3.1.3) split over P ranks by an owner hash: state t
+ * belongs to rank owner(t) = mix64(t) mod P (mix64: the 64-bit MurmurHash3 finaliser of the
+ * packed key).  Each rank expands its share of layer r, sends every candidate to its owner (one
+ * all-to-all of packed keys), and each owner keeps the candidates absent from its share of the
+ * visited states (cg_hash_insert); the new shares form layer r+1, whose size is the sum over
+ * ranks (one all-reduce).  The exchange itself is the caller's (the Python driver uses
+ * torch.distributed: NCCL on GPUs).
+ *
+ * cg_shard_owner    host only: owner(key) for P ranks (P >= 1), or CG_EINVAL.
+ * cg_shard_expand   expand frontier[0, F) (device, packed untagged keys, n <= 16) by the k
+ *                   generators (host, k*n bytes as for cg_growth_create, copied) and write the
+ *                   k*F candidates to out (device, cap >= k*F keys) grouped by owner: owner p's
+ *                   candidates are out[o_p, o_p + counts_out[p]), o_p = sum of the counts before
+ *                   p, in no particular order.  counts_out: host, P entries.  Waits for the
+ *                   stream.  Errors: CG_EINVAL (bad rows, P not in [1, 4096], cap too small),
+ *                   CG_ENOMEM, CG_ECUDA.
+ */
+int cg_shard_owner(uint64_t key, int P);
+int cg_shard_expand(int n, int k, const uint8_t* gens, const uint64_t* frontier, uint64_t F, int P,
+                    uint64_t* out, uint64_t cap, uint64_t* counts_out, void* cuda_stream);
 
 /* ---- step-level kernels (device pointers, asynchronous on the given stream) ----------- */
 

@@ -47,10 +47,12 @@ namespace {
 
 std::mutex g_mu;
 unsigned char* g_scratch_addr[64] = {};   // device address of g_noalloc_scratch, per device
-int g_grid[64] = {};
+int g_grid[64][5] = {};                   // co-resident blocks per device and probe ILP 1..4
 
 // Once per device, with that device current: the device address of the scratch array (the
-// array's name in host code is only a host-side stand-in, not a device address).
+// array's name in host code is only a host-side stand-in, not a device address).  The cached
+// address does not survive cudaDeviceReset: a process that resets a device must not call this
+// entry point on it again.
 int setup_device(int dev) {
     if (dev < 0 || dev >= 64) return CG_EINVAL;
     if (g_scratch_addr[dev]) return CG_OK;
@@ -60,10 +62,12 @@ int setup_device(int dev) {
         cudaGetLastError();
         return CG_ECUDA;
     }
-    const int grid = cg::hash_grow_max_grid(dev, 1, false);
-    if (grid <= 0) return CG_ECUDA;
+    for (int ilp = 1; ilp <= 4; ++ilp) {
+        const int grid = cg::hash_grow_max_grid(dev, ilp, false);
+        if (grid <= 0) return CG_ECUDA;
+        g_grid[dev][ilp] = grid;
+    }
     g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-    g_grid[dev] = grid;
     return CG_OK;
 }
 
@@ -82,17 +86,17 @@ bool row_is_identity(const uint8_t* g, int n) {
     return true;
 }
 
-bool has_inverse(const uint8_t* gens, int k, int n, int j) {
-    for (int m = 0; m < k; ++m) {
-        bool inv = true;
-        for (int i = 0; i < n && inv; ++i) inv = gens[m * n + gens[j * n + i]] == i;
-        if (inv) return true;
-    }
-    return false;
+bool rows_equal(const uint8_t* a, const uint8_t* b, int n) {
+    for (int i = 0; i < n; ++i)
+        if (a[i] != b[i]) return false;
+    return true;
 }
 
+// Shift-and-mask form of the gather t[i] = s[g[i]] on 4-bit elements (every permutation of
+// n <= 16 elements has at most 16 distinct offsets i - g[i]).
 void make_gensm(const uint8_t* g, int n, cg::GenSM& G) {
     std::memset(&G, 0, sizeof(G));
+    G.width = 4;
     for (int i = 0; i < n; ++i) {
         const unsigned rot = (unsigned)((4 * (i - (int)g[i]) + 64) & 63);
         uint32_t t = 0;
@@ -105,14 +109,65 @@ void make_gensm(const uint8_t* g, int n, cg::GenSM& G) {
     }
 }
 
-// Host staging for the uploads (the call holds g_mu while it uses them).
+// Host staging (the call holds g_mu while it uses them; fixed arrays, no heap): the distinct
+// non-identity rows and their device form.
+uint8_t g_rows[kMaxGens][cg::kMaxN];
 cg::GenSM g_host_gens[kMaxGens];
+
+// Distinct non-identity rows of gens into g_rows; returns their number, or -1 when there are
+// more than kMaxGens of them.
+int distinct_rows(const uint8_t* gens, int k, int n) {
+    int kk = 0;
+    for (int j = 0; j < k; ++j) {
+        const uint8_t* r = gens + (size_t)j * n;
+        if (row_is_identity(r, n)) continue;
+        bool dup = false;
+        for (int m = 0; m < kk && !dup; ++m) dup = rows_equal(g_rows[m], r, n);
+        if (dup) continue;
+        if (kk == kMaxGens) return -1;
+        std::memcpy(g_rows[kk++], r, n);
+    }
+    return kk;
+}
+
+// Each generator's parent-edge tag: 1 + index of its inverse among the rows when that index is
+// below 15 (the tag lives in key bits 60-63), else 0 (no skip).
+void set_inverse_tags(int kk, int n) {
+    for (int j = 0; j < kk; ++j) {
+        uint8_t inv[cg::kMaxN];
+        for (int i = 0; i < n; ++i) inv[g_rows[j][i]] = (uint8_t)i;
+        g_host_gens[j].inv_tag = 0;
+        for (int m = 0; m < kk && m < 15; ++m)
+            if (rows_equal(g_rows[m], inv, n)) { g_host_gens[j].inv_tag = (uint32_t)(m + 1); break; }
+    }
+}
+
+bool closed_under_inverse(int kk, int n) {
+    for (int j = 0; j < kk; ++j) {
+        uint8_t inv[cg::kMaxN];
+        for (int i = 0; i < n; ++i) inv[g_rows[j][i]] = (uint8_t)i;
+        bool found = false;
+        for (int m = 0; m < kk && !found; ++m) found = rows_equal(g_rows[m], inv, n);
+        if (!found) return false;
+    }
+    return true;
+}
 
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return CG_OK;
     cudaGetLastError();
     return CG_ECUDA;
 }
+
+// Once work is enqueued on the stream, every return waits for it first: the shared array must
+// be idle when the next call (possibly on another stream) takes the lock.
+struct StreamDrain {
+    cudaStream_t st;
+    bool armed = false;
+    ~StreamDrain() {
+        if (armed && cudaStreamSynchronize(st) != cudaSuccess) cudaGetLastError();
+    }
+};
 
 }  // namespace
 
@@ -121,22 +176,21 @@ extern "C" int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inve
                                      uint64_t* layer_sizes_out, int cap, int* num_layers_out) {
     if (n < 1 || n > cg::kMaxN || k < 1 || !gens || !layer_sizes_out || !num_layers_out || cap < 1)
         return CG_EINVAL;
-    if (k > kMaxGens) return CG_ETOOBIG;
     for (int j = 0; j < k; ++j)
-        if (!row_is_perm(gens + j * n, n)) return CG_EINVAL;
-    if (inverse_closed)
-        for (int j = 0; j < k; ++j)
-            if (!has_inverse(gens, k, n, j)) return CG_ENOTCLOSED;
+        if (!row_is_perm(gens + (size_t)j * n, n)) return CG_EINVAL;
 
     std::lock_guard<std::mutex> lock(g_mu);
-    int kk = 0;
-    for (int j = 0; j < k; ++j)
-        if (!row_is_identity(gens + j * n, n)) make_gensm(gens + j * n, n, g_host_gens[kk++]);
+    // identity rows add no edge and duplicates add none either; the limit counts distinct rows
+    const int kk = distinct_rows(gens, k, n);
+    if (kk < 0) return CG_ETOOBIG;
+    if (inverse_closed && !closed_under_inverse(kk, n)) return CG_ENOTCLOSED;
     if (kk == 0 || max_radius == 0) {
         *num_layers_out = 1;
         layer_sizes_out[0] = 1;
         return kk == 0 ? CG_OK : CG_TRUNC_RADIUS;
     }
+    for (int j = 0; j < kk; ++j) make_gensm(g_rows[j], n, g_host_gens[j]);
+    set_inverse_tags(kk, n);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -167,16 +221,29 @@ extern "C" int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inve
     J.max_radius = max_radius < 0 ? -1 : max_radius;
     J.tagged = n <= 15 ? 1 : 0;
 
+    // Probe ILP and grid as the allocating path chooses them for a hash table: all generators
+    // in flight up to 4, and fewer blocks for small groups (at most n! states, which is also
+    // the bound for any subgroup), so that a small growth does not pay a barrier across every
+    // co-resident block on each layer.
+    const int ilp = kk < 4 ? kk : 4;
+    uint64_t bound = 1;
+    for (int i = 2; i <= n && bound < kMaxStates; ++i) bound *= (uint64_t)i;
+    if (bound > kMaxStates) bound = kMaxStates;
+    const uint64_t want = bound / 512 + 1;
+    const int grid = (int)(want < (uint64_t)g_grid[dev][ilp] ? want : (uint64_t)g_grid[dev][ilp]);
+
     // Everything the kernels read first is rewritten here: the visited table is emptied, the
     // control block zeroed, the job and generators uploaded.
+    StreamDrain drain{st};
+    drain.armed = true;
     if ((e = cudaMemcpyAsync(d_gens, g_host_gens, sizeof(cg::GenSM) * kk, cudaMemcpyHostToDevice, st)))
         return cuda_rc(e);
     if ((e = cudaMemcpyAsync(d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st))) return cuda_rc(e);
     if ((e = cudaMemsetAsync(table, 0xFF, kTableSlots * 8, st))) return cuda_rc(e);
     if ((e = cudaMemsetAsync(d_ctl, 0, sizeof(cg::Ctl), st))) return cuda_rc(e);
     if ((e = cg::launch_init_jobs(d_job, 1, d_ubeg, d_ctl, st))) return cuda_rc(e);
-    if ((e = cg::launch_hash_grow(d_job, 1, d_ubeg, d_ctl, g_grid[dev], cg::kMaxLayers + 1,
-                                  kTimeoutNs, 1, st)))
+    if ((e = cg::launch_hash_grow(d_job, 1, d_ubeg, d_ctl, grid, cg::kMaxLayers + 1, kTimeoutNs,
+                                  ilp, st)))
         return cuda_rc(e);
     cg::Ctl ctl;
     if ((e = cudaMemcpyAsync(&J, d_job, sizeof(J), cudaMemcpyDeviceToHost, st))) return cuda_rc(e);
@@ -190,6 +257,7 @@ extern "C" int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inve
     if ((e = cudaMemcpyAsync(layer_sizes_out, layers, sizeof(uint64_t) * nl, cudaMemcpyDeviceToHost, st)))
         return cuda_rc(e);
     if ((e = cudaStreamSynchronize(st))) return cuda_rc(e);
+    drain.armed = false;
     switch (J.status) {
         case cg::kDone: return CG_OK;
         case cg::kTruncRadius: return CG_TRUNC_RADIUS;
