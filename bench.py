@@ -117,8 +117,36 @@ def algorithmic_bytes(layers, k, complete):
 
 
 def neighbours(layers, k, complete):
+    """The metric's unit count: the graph's edges out of every expanded layer, k * sum F_r."""
     expanded = len(layers) if complete else len(layers) - 1
     return k * sum(layers[:expanded])
+
+
+def generated_candidates(n, gens, layers, complete, skips_parent):
+    """Candidates the kernels actually generate and probe.  The key-list strategies (bitmap and
+    hash) store a state found through generator g with the tag of g's inverse and do not expand
+    that edge (it leads back to the parent): when every distinct generator's inverse is in the
+    set among its first 15 rows and n <= 15, each state after the first skips one generator.
+    None when only some generators have their inverse there (the count depends on the path)."""
+    expanded = len(layers) if complete else len(layers) - 1
+    rows = []
+    for g in gens:
+        t = tuple(int(x) for x in g)
+        if t != tuple(range(n)) and t not in rows:
+            rows.append(t)
+    k = len(rows)
+    total = k * sum(layers[:expanded])
+    if not skips_parent or n > 15 or expanded == 0:
+        return total
+    def inv(t):
+        r = [0] * len(t)
+        for i, v in enumerate(t):
+            r[v] = i
+        return tuple(r)
+    tagged = [inv(t) in rows[:15] for t in rows]
+    if all(tagged):
+        return total - sum(layers[1:expanded])
+    return total if not any(tagged) else None
 
 
 class ClockSampler:
@@ -407,6 +435,12 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": job.name, "n": job.n, "k": job.k, "states": sum(layers),
                    "layers": len(layers), "neighbours_per_step": nb_step,
+                   "generated_per_step": generated_candidates(job.n, job.gens, layers, complete,
+                                                              strat_name in ("bitmap", "hash")),
+                   "counting": "value and roofline count k * sum F_r neighbours (every edge out of "
+                               "every expanded layer) and the algorithmic bytes of that growth; "
+                               "generated_per_step is what the kernel expands after skipping each "
+                               "state's parent edge",
                    "strategy": strat_name + {
                        "sort": " (sorted layers: expand, radix sort, merge-path difference)",
                        "sweep": " (bitmaps over S_n for the visited set and layers; one persistent "
@@ -431,6 +465,8 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, job)
+    if world == 1 and not args.no_extra and args.workload == "s11_lrx" and args.strategy == "auto":
+        out["extra"] = extra_configs(cg, stream, flush)
     print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
@@ -440,6 +476,53 @@ def run_ours(args):
 
 # --------------------------------------------------------------------------------------------
 # Config 4: 4096 independent random groups, one persistent launch per batch run
+
+def measure_batch(cg, spec, stream, flush, steps, warmup, autotune=True, tune_table=None):
+    """Time batched runs of `spec` (jobs as for Batch): optionally autotuned first (outside the
+    timed region), then `warmup` untimed and `steps` timed runs with L2 flushed between them."""
+    import torch
+    tuned = None
+    if autotune:
+        from paper_2509_19162_gb300 import tune
+        t0 = time.perf_counter()
+        table = tune.TuneTable(tune_table) if tune_table else None
+        tuned = tune.tune_batch(spec, stream=stream, table=table)
+        tuned["tuning_s"] = time.perf_counter() - t0
+    batch = cg.Batch(spec, **(tuned["options"] if tuned else {}))
+    res = None
+    for _ in range(max(1, warmup)):
+        res = batch.run(stream)
+    layers = [r.layers for r in res]
+    total_ms, kernel_ms, launches = 0.0, 0.0, 0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = batch.run(stream)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        st = batch.stats()
+        kernel_ms += st["kernel_ms"]
+        launches += st["launches"]
+        if [r.layers for r in out] != layers:
+            raise RuntimeError("batched layer counts changed between steps")
+    variant = batch.stats()["probe_variant"]
+    batch.close()
+    return {"layers": layers, "statuses": [r.status for r in res], "total_ms": total_ms,
+            "kernel_ms": kernel_ms, "launches": launches, "variant": variant, "tuned": tuned}
+
+
+def one_at_a_time(cg, jobs, stream, mem_cap=0):
+    """Jobs run one after another through growth() on the same GPU: (layers, seconds)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = [cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=mem_cap, stream=stream).layers
+           for j in jobs]
+    return out, time.perf_counter() - t0
+
 
 def run_batch(args):
     import torch
@@ -455,21 +538,6 @@ def run_batch(args):
     spec = [(j.n, j.gens, j.inverse_closed, -1) for j in jobs]
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-    tuned = None
-    if not args.no_autotune:
-        # launch settings picked by the autotuner on this batch (outside the timed region)
-        from paper_2509_19162_gb300 import tune
-        t0 = time.perf_counter()
-        table = tune.TuneTable(args.tune_table) if args.tune_table else None
-        tuned = tune.tune_batch(spec, stream=stream, table=table)
-        tuned["tuning_s"] = time.perf_counter() - t0
-    batch = cg.Batch(spec, **(tuned["options"] if tuned else {}))
-    res = None
-    for _ in range(args.warmup):
-        res = batch.run(stream)
-    layers = [r.layers for r in res]
-    nb_step = sum(len(j.gens) * sum(l) for j, l in zip(jobs, layers))
-    bytes_step = sum(algorithmic_bytes(l, len(j.gens), True) for j, l in zip(jobs, layers))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -477,25 +545,14 @@ def run_batch(args):
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
-    total_ms, kernel_ms, launches = 0.0, 0.0, 0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        out = batch.run(stream)
-        b.record(stream)
-        b.synchronize()
-        total_ms += a.elapsed_time(b)
-        st = batch.stats()
-        kernel_ms += st["kernel_ms"]
-        launches += st["launches"]
-        if [r.layers for r in out] != layers:
-            raise RuntimeError("batched layer counts changed between steps")
+    m = measure_batch(cg, spec, stream, flush, args.steps, args.warmup, not args.no_autotune,
+                      args.tune_table)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
-    variant = batch.stats()["probe_variant"]
-    batch.close()
+    layers, tuned, launches = m["layers"], m["tuned"], m["launches"]
+    nb_step = sum(len(j.gens) * sum(l) for j, l in zip(jobs, layers))
+    bytes_step = sum(algorithmic_bytes(l, len(j.gens), True) for j, l in zip(jobs, layers))
+    total_ms = m["total_ms"]
     if world > 1:
         total_ms, nb_all = combine_ranks(total_ms, nb_step)
     else:
@@ -510,15 +567,13 @@ def run_batch(args):
     e2e_s = time.perf_counter() - t0
     # one at a time, same GPU, first 512 groups of this rank's share (same results required)
     sample = jobs[:512]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    single = [cg.growth(j.n, j.gens, j.inverse_closed, stream=stream).layers for j in sample]
-    one_s = time.perf_counter() - t0
+    single, one_s = one_at_a_time(cg, sample, stream)
     if single != layers[:len(sample)]:
         raise RuntimeError("one-at-a-time results differ from the batched results")
     peak, peak_kind = load_peaks()
-    kms = kernel_ms / args.steps
+    kms = m["kernel_ms"] / args.steps
     achieved = bytes_step / (kms / 1000.0) / 1e9
+    variant = m["variant"]
     if rank != 0:
         return 0
     out = {
@@ -542,8 +597,8 @@ def run_batch(args):
             "traffic": measured_traffic(f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0>",
                                         f"batched-{len(jobs_all)}-random-groups-seed{wl.BATCH_SEED}",
                                         tuned["settings"] if tuned else None),
-            "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0> (multi-job, "
-                      f"{launches // (3 * args.steps)} launches per batch run)",
+            "kernel": f"hash_grow_kernel<{variant & 7}, {variant >> 3}, 1, 0> (multi-job, one "
+                      f"persistent launch per batch run admitting the jobs by the L2 window)",
             "kernel_ms": kms, "algorithmic_bytes": bytes_step, "peak_source": peak_kind}),
         "e2e": {"value": nb_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": est["h2d_bytes"],
                 "d2h_bytes_per_step": est["d2h_bytes"], "api": "paper_2509_19162_gb300.Batch(...).run()"},
@@ -556,57 +611,131 @@ def run_batch(args):
 # --------------------------------------------------------------------------------------------
 # Config 5: Poisson stream of growth jobs through the continuous-batching server
 
-def run_serve(args):
-    import torch
+SERVE_BUDGET = 160 << 30
+
+
+def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=4, job_mem=0, lam_sample=200):
+    """Serve `jobs` at multiples of the one-at-a-time capacity lambda_1 (measured first on the
+    same GPU, each job alone with the same per-job share).  job_mem = 0: the server's default
+    share of the 160 GiB budget (budget / 64).  Returns (lambda_1, [one summary per rate])."""
     import numpy as np
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    import paper_2509_19162_gb300 as cg
     from paper_2509_19162_gb300.serve import Server, serve_stream
-    cg.build()
-    jobs = wl.serve_stream(count=args.serve_jobs)
-    stream = torch.cuda.Stream()
-    budget = 160 << 30
-    job_cap = args.serve_job_mem << 20
-    # one at a time on the same GPU (each job alone, same per-job memory cap): capacity lambda_1
-    sample = jobs[:200]
-    for j in sample[:20]:
-        cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=job_cap, stream=stream)
-    t0 = time.perf_counter()
-    for j in sample:
-        cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=job_cap, stream=stream)
-    lam1 = len(sample) / (time.perf_counter() - t0)
-    lines = []
-    for mult in (1.0, 2.0, 4.0):
+    share = job_mem or SERVE_BUDGET // 64
+    plans = [Server.predict(j.n, j.gens, j.inverse_closed, j.max_radius, job_mem_cap=share) for j in jobs]
+    over = [i for i, p in enumerate(plans) if p["granted"] < p["states"]]
+    sample = jobs[:lam_sample]
+    one_at_a_time(cg, sample[:10], stream, mem_cap=share)
+    _, one_s = one_at_a_time(cg, sample, stream, mem_cap=share)
+    lam1 = len(sample) / one_s
+    out = []
+    for mult in rates:
         lam = lam1 * mult
         arr = [j.arrival / lam for j in jobs]
-        with Server(mem_budget=budget, max_slots=args.serve_slots, job_mem_cap=job_cap,
-                    rounds_per_step=args.serve_rounds) as srv:
+        with Server(mem_budget=SERVE_BUDGET, max_slots=slots, job_mem_cap=share,
+                    rounds_per_step=rounds) as srv:
             sampler = ClockSampler(0)
             sampler.start()
             rep = serve_stream(jobs, arr, srv, stream)
             clocks = sampler.stop()
         statuses = [r.status for r in rep.results]
-        lines.append({
-            "metric": "jobs/sec + p50/p99 latency (serving)", "value": rep.jobs_per_s, "unit": "jobs/s",
-            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": rep.makespan_s * 1000.0,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic",
-            "config": {"workload": f"serving-{len(jobs)}-jobs-seed{wl.SERVE_SEED}", "arrival_rate_jobs_per_s": lam,
-                       "rate": f"{mult:g} x one-at-a-time capacity ({lam1:.1f} jobs/s)",
-                       "mem_budget_gib": budget >> 30, "job_mem_cap_mib": args.serve_job_mem,
-                       "slots": args.serve_slots, "rounds_per_step": args.serve_rounds,
-                       "server_steps": rep.steps, "max_active": rep.max_active,
-                       "mean_active": rep.mean_active,
-                       "ended": {"complete": statuses.count(0), "radius_cap": statuses.count(1),
-                                 "mem_cap": statuses.count(2)}},
+        memcap_ended = [i for i, st in enumerate(statuses) if st == 2]
+        out.append({
+            "rate": f"{mult:g} x one-at-a-time capacity", "arrival_rate_jobs_per_s": lam,
+            "jobs_per_s": rep.jobs_per_s, "makespan_s": rep.makespan_s,
             "latency_ms": {"p50": rep.percentile_ms(50), "p99": rep.percentile_ms(99),
                            "mean": float(np.mean(rep.latency_s) * 1000.0)},
-            "one_at_a_time_jobs_per_s": lam1,
-            "clocks": clocks,
-        })
-    for ln in lines:
-        print(json.dumps(ln))
+            "server_steps": rep.steps, "max_active": rep.max_active, "mean_active": rep.mean_active,
+            "ended": {"complete": statuses.count(0), "radius_cap": statuses.count(1),
+                      "mem_cap": statuses.count(2)},
+            # every job stopped by memory is one whose predicted states exceed its share
+            "mem_cap_all_predicted_over_share": set(memcap_ended) <= set(over),
+            "clocks": clocks})
+    return lam1, {"jobs": len(jobs), "job_share_bytes": share, "budget_bytes": SERVE_BUDGET,
+                  "predicted_over_share": len(over), "predicted_over_share_ids": over[:50]}, out
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2509_19162_gb300 as cg
+    cg.build()
+    jobs = wl.serve_stream(count=args.serve_jobs)
+    stream = torch.cuda.Stream()
+    lam1, info, rates = measure_serve(cg, jobs, stream, rates=(1.0, 2.0, 4.0), slots=args.serve_slots,
+                                      rounds=args.serve_rounds, job_mem=args.serve_job_mem << 20)
+    for r in rates:
+        print(json.dumps({
+            "metric": "jobs/sec + p50/p99 latency (serving)", "value": r["jobs_per_s"], "unit": "jobs/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": r["makespan_s"] * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"serving-{len(jobs)}-jobs-seed{wl.SERVE_SEED}", **info,
+                       "slots": args.serve_slots, "rounds_per_step": args.serve_rounds,
+                       **{k: v for k, v in r.items() if k not in ("jobs_per_s", "latency_ms", "clocks")}},
+            "latency_ms": r["latency_ms"], "one_at_a_time_jobs_per_s": lam1, "clocks": r["clocks"]}))
     return 0
+
+
+# --------------------------------------------------------------------------------------------
+# The other configurations, measured briefly beside the default line (its `extra`)
+
+def quick_growth(cg, job, stream, flush, steps=3, warmup=2):
+    """A few timed runs of one growth: rate, time per run, kernel time and its HBM fraction."""
+    import torch
+    with cg.Growth(job.n, job.gens, job.inverse_closed, job.max_radius, stop_above=job.stop_above,
+                   start=job.start) as g:
+        for _ in range(warmup):
+            r = g.run(stream)
+        ms, kms = [], []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r2 = g.run(stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            kms.append(g.stats()["kernel_ms"])
+            if r2.layers != r.layers:
+                raise RuntimeError("layer counts changed between steps")
+        st = g.stats()
+    complete = r.status == 0
+    nb = neighbours(r.layers, job.k, complete)
+    peak, _ = load_peaks()
+    t, kt = statistics.median(ms), statistics.median(kms)
+    return {"workload": job.name, "value": nb / (t / 1000.0), "unit": UNIT, "ms_per_step": t,
+            "kernel_ms": kt, "layers": len(r.layers), "states": sum(r.layers), "status": r.status,
+            "strategy": {1: "hash", 2: "sort", 3: "bitmap", 4: "sweep"}.get(st["strategy_used"], "?"),
+            "roofline_frac": algorithmic_bytes(r.layers, job.k, complete) / (kt / 1000.0) / 1e9 / peak,
+            "steps": steps}
+
+
+def extra_configs(cg, stream, flush):
+    """Configs 1, 3, 4 and 5 measured briefly (the default line's value stays config 2)."""
+    out = {"config1": quick_growth(cg, wl.config_s8_coxeter(), stream, flush, steps=10, warmup=3),
+           "config3": quick_growth(cg, wl.config_s14_pancake(), stream, flush, steps=3, warmup=1)}
+    jobs = wl.batch_groups()
+    spec = [(j.n, j.gens, j.inverse_closed, -1) for j in jobs]
+    m = measure_batch(cg, spec, stream, flush, steps=3, warmup=2, autotune=False)
+    single, one_s = one_at_a_time(cg, jobs[:256], stream)
+    if single != m["layers"][:256]:
+        raise RuntimeError("one-at-a-time results differ from the batched results")
+    t = m["total_ms"] / 3
+    jps = len(jobs) / (t / 1000.0)
+    out["config4"] = {"workload": f"batched-{len(jobs)}-random-groups-seed{wl.BATCH_SEED}",
+                      "value": sum(len(j.gens) * sum(l) for j, l in zip(jobs, m["layers"])) / (t / 1000.0),
+                      "unit": UNIT, "ms_per_step": t, "jobs_per_s": jps,
+                      "one_at_a_time_jobs_per_s": 256 / one_s,
+                      "batched_over_one_at_a_time": jps / (256 / one_s),
+                      "launches_per_run": m["launches"] // 3, "settings": "library defaults",
+                      "all_complete": all(s == 0 for s in m["statuses"])}
+    sjobs = wl.serve_stream(count=1000)
+    lam1, info, rates = measure_serve(cg, sjobs, stream, rates=(1.0, 2.0), lam_sample=100)
+    out["config5"] = {"workload": f"serving-first-1000-of-20000-jobs-seed{wl.SERVE_SEED}", **info,
+                      "one_at_a_time_jobs_per_s": lam1,
+                      "rates": [{k: v for k, v in r.items() if k != "clocks"} for r in rates]}
+    return out
 
 
 def main():
@@ -619,6 +748,8 @@ def main():
                     help="s11_lrx | s8_coxeter | s14_pancake | batch | serve | <family>:<n> "
                          "(full growth of a named family, e.g. pancake:14)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the brief runs of configs 1, 3, 4 and 5 (extra)")
     ap.add_argument("--strategy", default="auto", choices=["auto", "hash", "bitmap", "sort", "sweep"],
                     help="visited-set strategy of the single-job workloads")
     ap.add_argument("--sweep-order", default="auto", choices=["auto", "discovery", "rank"],
@@ -627,7 +758,8 @@ def main():
                     help="batch workload: run with the library's default launch settings")
     ap.add_argument("--tune-table", default=None, help="JSON file to record tuned settings in")
     ap.add_argument("--serve-jobs", type=int, default=20000)
-    ap.add_argument("--serve-job-mem", type=int, default=64, help="per-job device memory cap, MiB")
+    ap.add_argument("--serve-job-mem", type=int, default=0,
+                    help="per-job device memory share, MiB (0: the server default, budget / 64)")
     ap.add_argument("--serve-slots", type=int, default=512)
     ap.add_argument("--serve-rounds", type=int, default=4)
     args = ap.parse_args()

@@ -32,6 +32,8 @@ CG_STRATEGY_SWEEP = 4
 CG_OPT_BATCH_WAVE_L2 = 6
 CG_OPT_BATCH_VISITED = 7
 CG_OPT_GRAPH = 8
+CG_OPT_BATCH_ACTIVE = 10
+CG_OPT_UNIT = 11
 
 CG_OPT_STRATEGY = 1
 CG_OPT_STOP_ABOVE = 2
@@ -72,6 +74,7 @@ SIGNATURES = {
     "cg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "cg_last_error_detail": (ctypes.c_char_p, []),
     "cg_growth_key_width": (ctypes.c_int, [_vp]),
+    "cg_growth_key_words": (ctypes.c_int, [_vp]),
     "cg_batch_create": (ctypes.c_int, [ctypes.c_int, _ip, _ip, _u8p, _u64p, _ip, _ip, ctypes.c_uint64,
                                        ctypes.POINTER(_vp)]),
     "cg_batch_run": (ctypes.c_int, [_vp, _vp, _u64p, ctypes.c_int, _ip, _ip]),
@@ -82,6 +85,8 @@ SIGNATURES = {
     "cg_server_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.POINTER(_vp)]),
     "cg_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int, _u64p]),
+    "cg_server_predict": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_uint64, _u64p, _u64p, _u64p]),
     "cg_server_step": (ctypes.c_int, [_vp, _vp, _ip, _ip]),
     "cg_server_finished": (ctypes.c_int, [_vp, _u64p, ctypes.c_int, _ip]),
     "cg_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _u64p, ctypes.c_int, _ip, _ip]),
@@ -92,6 +97,9 @@ SIGNATURES = {
     "cg_expand": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_hash_insert": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp, _vp]),
     "cg_hash_clear": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp]),
+    "cg_shard_owner": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    "cg_shard_expand": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _vp, ctypes.c_uint64, ctypes.c_int,
+                                       _vp, ctypes.c_uint64, _u64p, _vp]),
     "cg_perm_rank": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_perm_unrank": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_uint64, _vp, _vp]),
     "cg_sort_unique_scratch_bytes": (ctypes.c_size_t, [ctypes.c_uint64]),
@@ -151,6 +159,7 @@ cg_growth_destroy = _export("cg_growth_destroy")
 cg_strerror = _export("cg_strerror")
 cg_last_error_detail = _export("cg_last_error_detail")
 cg_growth_key_width = _export("cg_growth_key_width")
+cg_growth_key_words = _export("cg_growth_key_words")
 cg_batch_create = _export("cg_batch_create")
 cg_batch_run = _export("cg_batch_run")
 cg_batch_destroy = _export("cg_batch_destroy")
@@ -161,6 +170,7 @@ cg_perm_rank = _export("cg_perm_rank")
 cg_perm_unrank = _export("cg_perm_unrank")
 cg_server_create = _export("cg_server_create")
 cg_server_submit = _export("cg_server_submit")
+cg_server_predict = _export("cg_server_predict")
 cg_server_step = _export("cg_server_step")
 cg_server_finished = _export("cg_server_finished")
 cg_server_result = _export("cg_server_result")
@@ -170,6 +180,8 @@ cg_growth_run_noalloc = _export("cg_growth_run_noalloc")
 cg_expand = _export("cg_expand")
 cg_hash_insert = _export("cg_hash_insert")
 cg_hash_clear = _export("cg_hash_clear")
+cg_shard_owner = _export("cg_shard_owner")
+cg_shard_expand = _export("cg_shard_expand")
 cg_sort_unique_scratch_bytes = _export("cg_sort_unique_scratch_bytes")
 cg_sort_unique = _export("cg_sort_unique")
 cg_set_difference = _export("cg_set_difference")

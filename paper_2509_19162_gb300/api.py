@@ -189,12 +189,22 @@ class Growth:
         return {f: getattr(st, f) for f, _ in st._fields_}
 
     def last_layer(self) -> np.ndarray:
+        """Packed keys of the last layer: shape (count,) uint64, or (count, 2) (low, high word)
+        for keys of more than 64 bits (key_words == 2)."""
         cnt = ctypes.c_uint64(0)
         _cg.cg_growth_last_layer(self._h, None, 0, ctypes.byref(cnt))
-        out = np.zeros(max(1, cnt.value), dtype=np.uint64)
+        words = self.key_words
+        out = np.zeros(max(1, cnt.value) * words, dtype=np.uint64)
         _cg.check(_cg.cg_growth_last_layer(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                            cnt.value, ctypes.byref(cnt)), "cg_growth_last_layer")
+        if words == 2:
+            return out[:2 * cnt.value].reshape(cnt.value, 2)
         return out[:cnt.value]
+
+    @property
+    def key_words(self) -> int:
+        """64-bit words per packed key (2 for vectors of more than 64 bits)."""
+        return int(_cg.cg_growth_key_words(self._h))
 
     @property
     def key_width(self) -> int:
@@ -205,6 +215,17 @@ class Growth:
         """The last layer as an array of shape (count, n): the unpacked states."""
         keys = self.last_layer()
         w = self.key_width
+        if keys.ndim == 2:                     # two words: element i at bits [w i, w i + w)
+            out = np.zeros((keys.shape[0], self.n), dtype=np.uint8)
+            for i in range(self.n):
+                b = w * i
+                v = np.zeros(keys.shape[0], dtype=np.uint64)
+                for q in range(w):
+                    bit = b + q
+                    word = keys[:, bit // 64]
+                    v |= ((word >> np.uint64(bit % 64)) & np.uint64(1)) << np.uint64(q)
+                out[:, i] = v.astype(np.uint8)
+            return out
         shifts = (w * np.arange(self.n, dtype=np.uint64)).astype(np.uint64)
         return ((keys[:, None] >> shifts[None, :]) & np.uint64((1 << w) - 1)).astype(np.uint8)
 
@@ -241,11 +262,14 @@ class Batch:
     VISITED = {"auto": _cg.CG_STRATEGY_AUTO, "hash": _cg.CG_STRATEGY_HASH, "bitmap": _cg.CG_STRATEGY_BITMAP}
 
     def __init__(self, jobs, mem_cap: int = 0, wave_l2: Optional[int] = None, ilp: int = 0,
-                 grid: int = 0, visited: str = "auto", graph: bool = False):
+                 grid: int = 0, visited: str = "auto", graph: bool = True, max_active: int = 0,
+                 unit: int = 4):
         """jobs: sequence of (n, gens, inverse_closed, max_radius).
-        wave_l2: cap on the summed visited-set bytes grown in one launch (None or 0: half of L2;
-        -1: no cap).  ilp, grid: kernel variant and blocks of the launches (0: library choice).
-        visited: "auto", "hash" or "bitmap".  graph: capture a whole run as a CUDA graph."""
+        wave_l2: cap on the summed visited-set bytes of the jobs grown at once (None or 0: half
+        of L2; -1: no cap).  ilp, grid: kernel variant and blocks of the launch (0: library
+        choice).  visited: "auto", "hash" or "bitmap".  graph: capture a whole run as a CUDA
+        graph (default).  max_active: most jobs grown at once (0: library choice).  unit:
+        frontier states per warp work unit, in multiples of 32 (1, 2, 4 or 8; default 4)."""
         self.njobs = len(jobs)
         ns = np.array([j[0] for j in jobs], dtype=np.int32)
         ks = np.array([len(j[1]) for j in jobs], dtype=np.int32)
@@ -266,13 +290,19 @@ class Batch:
                                       ctypes.byref(h)), "cg_batch_create")
         self._h = h
         self._out = None
-        self.set_options(wave_l2=wave_l2 or 0, ilp=ilp, grid=grid, visited=visited, graph=graph)
+        self.set_options(wave_l2=wave_l2 or 0, ilp=ilp, grid=grid, visited=visited, graph=graph,
+                         max_active=max_active, unit=unit)
 
     def set_options(self, wave_l2: Optional[int] = None, ilp: Optional[int] = None,
                     grid: Optional[int] = None, visited: Optional[str] = None,
-                    graph: Optional[bool] = None) -> None:
+                    graph: Optional[bool] = None, max_active: Optional[int] = None,
+                    unit: Optional[int] = None) -> None:
         """Change launch settings (None: unchanged); see __init__."""
         opts = []
+        if max_active is not None:
+            opts.append((_cg.CG_OPT_BATCH_ACTIVE, int(max_active)))
+        if unit is not None:
+            opts.append((_cg.CG_OPT_UNIT, int(unit)))
         if wave_l2 is not None:
             opts.append((_cg.CG_OPT_BATCH_WAVE_L2, int(wave_l2)))
         if ilp is not None:

@@ -33,6 +33,59 @@ struct GenSM {
     uint64_t mask[kMaxTerms];
 };
 
+// Keys of more than 64 bits (two words): vectors of n elements of w bits with 64 < n w <= 128 --
+// coset vectors of 4-bit values up to n = 32, 2-bit up to 64, 1-bit up to 128, and permutations
+// of 17..25 elements from the identity with 5-bit elements.  Element i occupies bits
+// [w i, w i + w) of the 128-bit number hi:lo.
+struct alignas(16) Key128 {
+    uint64_t lo, hi;
+};
+
+constexpr int kMaxWideElems = 128;
+constexpr int kMaxWideTerms = 32;
+
+// A generator acting on two-word keys: kind 0 is the shift-and-mask form over 128 bits (one term
+// per distinct element offset, at most kMaxWideTerms); kind 1 the reversal of the element range
+// covered by mask (bit-reverse the 128-bit key, put each element's bits back in order, shift by
+// rev_shift bits: right if positive).
+struct WideGen {
+    uint32_t nterms;
+    uint32_t inv_tag;   // 1 + index of the inverse (< 15), or 0
+    uint8_t kind;
+    uint8_t width;
+    int16_t rev_shift;
+    uint8_t rot[kMaxWideTerms];
+    uint64_t mlo[kMaxWideTerms];
+    uint64_t mhi[kMaxWideTerms];
+};
+
+// One growth with two-word keys (hash strategy): every layer back to back in `keys`, the visited
+// set an open-addressing table of 16-byte slots (empty = all ones).  A state found by generator g
+// carries the tag (1 + index of g's inverse) in bits 124-127 when n w <= 124.
+struct alignas(128) WideDev {
+    Key128* keys;
+    uint64_t keys_cap;
+    Key128* table;
+    uint64_t table_mask;
+    const WideGen* gens;
+    uint64_t* layer_sizes;
+    uint64_t stop_above;
+    Key128 start;
+    int k;
+    int n;
+    int layers_cap;
+    int max_radius;
+    int tagged;
+    int pad0;
+    alignas(128) unsigned long long lo;     // frontier = keys[lo, hi)
+    unsigned long long hi;
+    unsigned long long tail;
+    int radius;
+    int status;
+    int overflow;
+    int pad1;
+};
+
 // States found by generator j are stored with tag (1 + index of j's inverse) in key bits 60-63
 // when the key leaves them free (n * width <= 60): that inverse leads back to the state's
 // parent, in the previous layer, so the expansion skips it.  The visited set always holds
@@ -119,6 +172,21 @@ struct alignas(128) SweepDev {
     int status;                // JobStatus
 };
 
+// Admission of many jobs into one persistent launch (a batch): the jobs are grown in index
+// order, at most max_active at a time and with the visited sets of the active jobs summing to at
+// most `window` bytes, so that their random accesses stay in L2.  Whenever jobs end, the block
+// that closes the round admits the next ones and sets them up; a job whose visited set alone
+// exceeds the window is counted as 0 (it misses L2 wherever it runs).
+struct AdmitDev {
+    int* act[2];               // active job indices, double-buffered (Ctl::adm.act_sel selects)
+    const uint64_t* vis;       // per job: visited-set bytes counted against `window`
+    uint64_t window;
+    int max_active;            // capacity of each act[]; the unit table holds max_active + 1
+    int njobs;
+    int unit_mult;             // frontier states per warp work unit: 32 * unit_mult
+    int pad;
+};
+
 // Control block of the persistent kernel (device memory, zero-initialised by the host).
 // Blocks arrive at the grid barrier on kBarGroups group counters, the last of each group on
 // the top counter; every counter and the generation word that waiting blocks poll sit in
@@ -147,6 +215,13 @@ struct alignas(128) Ctl {
         unsigned int count;
         unsigned int pad[31];
     } group[kBarGroups];
+    // Admission of a batch into one launch (AdmitDev), updated by the block that closes a round.
+    struct alignas(128) Admit {
+        int act_sel;                    // AdmitDev::act[act_sel] lists the active jobs
+        int nactive;
+        unsigned long long next_admit;  // next job index to admit
+        unsigned long long vis_used;    // counted visited-set bytes of the active jobs
+    } adm;
 };
 
 }  // namespace cg

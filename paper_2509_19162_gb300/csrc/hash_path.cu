@@ -20,6 +20,8 @@
 
 namespace cg {
 
+__device__ void init_job(JobDev& J);
+
 namespace {
 
 constexpr int kGrowBlock = 256;
@@ -126,6 +128,158 @@ __device__ void close_round(JobDev* jobs, int njobs, unsigned long long* ubeg, C
         ctl->dyn_next = static_units(s_carry);
         atomicAdd(&ctl->rounds, 1);
     }
+}
+
+// Block-wide inclusive scan of one 64-bit value per thread (blockDim.x = kGrowBlock); returns
+// the inclusive prefix, *total the block's sum.  Called by every thread of the block.
+__device__ __forceinline__ unsigned long long block_scan_incl(unsigned long long v, unsigned long long* total) {
+    __shared__ unsigned long long s_part[kGrowBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s_part[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = lane < kGrowBlock / 32 ? s_part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kGrowBlock / 32) s_part[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long r = v + (wid ? s_part[wid - 1] : 0);
+    *total = s_part[kGrowBlock / 32 - 1];
+    __syncthreads();
+    return r;
+}
+
+// Phase B of a batch launch (AdmitDev), executed by the block that arrives last: close the
+// layer of every active job, drop the jobs that ended from the active list (order kept), admit
+// the next jobs while the window allows, set them up, and lay out the next round's work units
+// over the active list (ubeg[slot], ubeg[nactive] = total).  With no active job and none left
+// to admit the total is 0 and the launch ends.  Also run by one block before the launch
+// (admit_first_kernel) to admit the first jobs.
+__device__ void close_round_admit(JobDev* jobs, unsigned long long* ubeg, Ctl* ctl, const AdmitDev* A) {
+    __shared__ unsigned long long s_units, s_freed, s_used, s_next;
+    __shared__ int s_kept, s_new;
+    const int sel = ld_relaxed_int(&ctl->adm.act_sel);
+    const int nact = ld_relaxed_int(&ctl->adm.nactive);
+    const int* cur = A->act[sel];
+    int* nxt = A->act[sel ^ 1];
+    const unsigned long long per_unit = 32ull * (unsigned long long)A->unit_mult;
+    if (threadIdx.x == 0) { s_units = 0; s_freed = 0; s_kept = 0; }
+    __syncthreads();
+    for (int base = 0; base < nact; base += blockDim.x) {
+        const int a = base + threadIdx.x;
+        unsigned long long units = 0, keep = 0;
+        int j = -1;
+        if (a < nact) {
+            j = __ldcg(cur + a);
+            JobDev& J = jobs[j];
+            unsigned long long lo, hi, tail, rs;
+            asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(&J.lo));
+            asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(tail), "=l"(rs) : "l"(&J.tail));
+            const int overflow = ld_relaxed_int(&J.overflow);
+            int radius = (int)(unsigned)(rs & 0xffffffffull);
+            int status = (int)(unsigned)(rs >> 32);
+            (void)lo;
+            if (status == kRunning) {
+                volatile JobDev& V = jobs[j];
+                if (overflow) {
+                    status = kNeedMem;
+                } else {
+                    const unsigned long long fresh = tail - hi;
+                    if (fresh == 0) {
+                        status = kDone;
+                    } else {
+                        radius += 1;
+                        J.layer_sizes[radius] = fresh;
+                        V.radius = radius;
+                        V.lo = hi;
+                        V.hi = tail;
+                        if (J.max_radius >= 0 && radius >= J.max_radius) status = kTruncRadius;
+                        else if (J.stop_above > 0 && fresh > J.stop_above) status = kTruncAbove;
+                        else if (radius + 1 >= J.layers_cap) status = kTruncRadius;
+                        if (status == kRunning) units = (fresh + per_unit - 1) / per_unit;
+                    }
+                }
+                if (status != kRunning) V.status = status;
+            }
+            if (status == kRunning) keep = 1;
+            else atomicAdd(&s_freed, (unsigned long long)A->vis[j]);
+        }
+        unsigned long long tk = 0, tu = 0;
+        const unsigned long long pk = block_scan_incl(keep, &tk);
+        const unsigned long long pu = block_scan_incl(units, &tu);
+        if (keep) {
+            const int slot = s_kept + (int)(pk - 1);
+            nxt[slot] = j;
+            ubeg[slot] = s_units + pu - units;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { s_kept += (int)tk; s_units += tu; }
+        __syncthreads();
+    }
+    // admission, by warp 0: 32 candidates per step, in job order, while the window and the
+    // active list allow (a job is always admitted when nothing else is active)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned long long used = ld_relaxed_ull(&ctl->adm.vis_used) - s_freed;
+        unsigned long long next = ld_relaxed_ull(&ctl->adm.next_admit);
+        const int kept = s_kept;
+        int nnew = 0;
+        while (next < (unsigned long long)A->njobs && kept + nnew < A->max_active) {
+            const unsigned long long c = next + lane;
+            const bool valid = c < (unsigned long long)A->njobs && kept + nnew + lane < A->max_active;
+            const unsigned long long v = valid ? A->vis[c] : 0;
+            unsigned long long pre = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const bool fits = valid && (used + pre <= A->window || (kept + nnew == 0 && lane == 0));
+            const unsigned fail = __ballot_sync(0xffffffffu, !fits);
+            const int cnt = fail ? __ffs(fail) - 1 : 32;
+            if (lane < cnt) nxt[kept + nnew + lane] = (int)c;
+            if (cnt > 0) used += __shfl_sync(0xffffffffu, pre, cnt - 1);
+            next += (unsigned long long)cnt;
+            nnew += cnt;
+            if (cnt < 32) break;
+        }
+        if (lane == 0) {
+            s_used = used;
+            s_next = next;
+            s_new = nnew;
+        }
+    }
+    __syncthreads();
+    const int kept = s_kept, nnew = s_new;
+    // set up the admitted jobs: one work unit each (their frontier is the start state)
+    for (int i = threadIdx.x; i < nnew; i += blockDim.x) {
+        JobDev& J = jobs[nxt[kept + i]];
+        init_job(J);
+        ubeg[kept + i] = s_units + (unsigned long long)i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long total = s_units + (unsigned long long)nnew;
+        ubeg[kept + nnew] = total;
+        ctl->adm.vis_used = s_used;
+        ctl->adm.next_admit = s_next;
+        ctl->adm.nactive = kept + nnew;
+        ctl->adm.act_sel = sel ^ 1;
+        ctl->total_units = total;
+        ctl->dyn_next = static_units(total);
+        atomicAdd(&ctl->rounds, 1);
+        __threadfence();
+    }
+    __syncthreads();
 }
 
 // close_round for a launch with one job, by one thread (no block-wide scan).  Called by every
@@ -247,27 +401,39 @@ __device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDe
 // One unit = 32 frontier states (one per lane) of job J, every generator applied to each:
 // expand, insert-if-absent into the visited table, stage the winners.  kProbeILP generators
 // are handled together (that many independent probe sequences in flight per thread).
+// A state found through generator g carries the tag 1 + (index of g's inverse); that inverse
+// leads back to its parent, which is already visited.  When every active lane of the warp holds
+// a tagged state, each lane runs only the other k - 1 generators (the generator index depends on
+// the lane), so the parent edge costs neither a probe nor the expansion and index arithmetic.
 template <int kProbeILP, int kMode, int kN = 0>
 __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned long long idx,
                                         unsigned long long hi, uint64_t* buf, int& cnt, int lane,
                                         bool& overflow_seen, uint64_t s) {
     const bool active = idx < hi;
     const int n = J->n;
+    const bool tagged = J->tagged != 0;
     unsigned tag = 0;                       // 1 + generator that leads back to the parent
-    if (J->tagged) {
+    if (tagged) {
         tag = (unsigned)(s >> 60);
         s &= kKeyBits60;
     }
     const int k = J->k;
-    for (int g0 = 0; g0 < k; g0 += kProbeILP) {
-        const int ng = min(kProbeILP, k - g0);
+    const bool skip = tagged && __all_sync(0xffffffffu, !active || tag != 0);
+    const int iters = skip ? k - 1 : k;
+    for (int j0 = 0; j0 < iters; j0 += kProbeILP) {
+        const int ng = min(kProbeILP, iters - j0);
         uint64_t t[kProbeILP];
         int res[kProbeILP];
+        int gi[kProbeILP];
         unsigned vmask = 0;
 #pragma unroll
         for (int i = 0; i < kProbeILP; ++i) {
-            t[i] = (i < ng) ? apply_gen<kMode != kVisitBitmap>(gens[g0 + i], s) : 0;
-            if (active && i < ng && tag != (unsigned)(g0 + i + 1)) vmask |= 1u << i;
+            const int j = j0 + i;
+            // skipping: generators 0..tag-2 keep their slot, the rest move up by one (inactive
+            // lanes have tag 0 and take j + 1 <= k - 1)
+            gi[i] = (skip && (int)tag - 1 <= j) ? j + 1 : j;
+            t[i] = (i < ng) ? apply_gen<kMode != kVisitBitmap>(gens[gi[i]], s) : 0;
+            if (active && i < ng && tag != (unsigned)(gi[i] + 1)) vmask |= 1u << i;
         }
         if (kMode == kVisitBitmap)
             bitmap_insert_multi<kProbeILP, kN>(reinterpret_cast<unsigned*>(J->table), J->bitmap_words,
@@ -287,7 +453,7 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
         for (int i = 0; i < kProbeILP; ++i) {
             const unsigned fresh = __ballot_sync(0xffffffffu, res[i] == 1);
             if (res[i] == 1) {
-                const uint64_t itag = (J->tagged && i < ng) ? (uint64_t)gens[g0 + i].inv_tag << 60 : 0;
+                const uint64_t itag = tagged ? (uint64_t)gens[gi[i]].inv_tag << 60 : 0;
                 buf[cnt + __popc(fresh & lanemask_lt())] = t[i] | itag;
             }
             cnt += __popc(fresh);
@@ -367,7 +533,7 @@ constexpr int kSmemGens = 32;
 template <int kProbeILP, int kMode, bool kMulti, int kN = 0>
 __global__ void __launch_bounds__(kGrowBlock, kMode == 2 ? 4 : ((kMode == 1 && kProbeILP >= 3) ? 2 : 3))
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
-                 uint64_t timeout_ns) {
+                 uint64_t timeout_ns, const AdmitDev* adm) {
     __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
     __shared__ GenSM s_gens[kSmemGens];
     __shared__ unsigned long long s_unit;
@@ -384,6 +550,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
     // barrier word, so no block reloads them.  (Several jobs: the round's layout is read from
     // the control block each round.)
     __shared__ unsigned long long s_lo, s_hi, s_total, s_fresh;
+    __shared__ int s_nact, s_sel;
     if (threadIdx.x == 0 && !kMulti) {
         const bool running = ld_relaxed_int(&jobs[0].status) == kRunning;
         s_lo = ld_relaxed_ull(&jobs[0].lo);
@@ -391,8 +558,13 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
     }
 
     for (int round = 0; round < max_rounds; ++round) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_total = kMulti ? ld_relaxed_ull(&ctl->total_units) : (s_hi - s_lo + 31) >> 5;
+            if (kMulti && adm) {
+                s_nact = ld_relaxed_int(&ctl->adm.nactive);
+                s_sel = ld_relaxed_int(&ctl->adm.act_sel);
+            }
+        }
         __syncthreads();
         const unsigned long long total = s_total;
         const unsigned long long lo = s_lo, hi = s_hi;
@@ -415,6 +587,11 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
             unsigned long long lo = 0, hi = 0, u0 = 0;
             const unsigned long long ue = stat * (blockIdx.x + 1) / gridDim.x;
             unsigned long long pending = ~0ull;
+            // a batch launch (adm): units map to slots of the active list, 32 * unit_mult
+            // frontier states each; otherwise to jobs, 32 states each
+            const int nj = adm ? s_nact : njobs;
+            const int* act = adm ? adm->act[s_sel] : nullptr;
+            const int umult = adm ? adm->unit_mult : 1;
             // the block's range, then (large rounds) the shared half, two units per draw
             auto next_unit = [&]() -> unsigned long long {
                 const unsigned long long u = draw_unit(s_unit, lane);
@@ -433,23 +610,27 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                 return d;
             };
             for (unsigned long long u = next_unit(); u != ~0ull; u = next_unit()) {
-                const int j = find_job(ubeg, njobs, u);
-                if (j != cur) {
+                const int slot = find_job(ubeg, nj, u);
+                if (slot != cur) {
                     if (J) stage_flush(buf, cnt, J, lane);
-                    cur = j;
-                    J = jobs + j;
+                    cur = slot;
+                    J = jobs + (act ? __ldcg(act + slot) : slot);
                     lo = ld_relaxed_ull(&J->lo);
                     hi = ld_relaxed_ull(&J->hi);
-                    u0 = ld_relaxed_ull(ubeg + j);
+                    u0 = ld_relaxed_ull(ubeg + slot);
                 }
                 if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
-                const unsigned long long idx = lo + ((u - u0) << 5) + lane;
-                const uint64_t s0 = idx < hi ? __ldcg(J->keys + idx) : 0;
-                // In the rank-bitmap variant a launch may mix jobs of both visited-set kinds.
-                if (kMode == kVisitBitmap && J->mode != kVisitBitmap)
-                    do_unit<kProbeILP, kVisitHash>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
-                else
-                    do_unit<kProbeILP, kMode>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                for (int sub = 0; sub < umult; ++sub) {
+                    const unsigned long long first = lo + (((u - u0) * (unsigned long long)umult + sub) << 5);
+                    if (first >= hi) break;
+                    const unsigned long long idx = first + lane;
+                    const uint64_t s0 = idx < hi ? __ldcg(J->keys + idx) : 0;
+                    // In the rank-bitmap variant a launch may mix jobs of both visited-set kinds.
+                    if (kMode == kVisitBitmap && J->mode != kVisitBitmap)
+                        do_unit<kProbeILP, kVisitHash>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                    else
+                        do_unit<kProbeILP, kMode>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                }
             }
             if (J) stage_flush(buf, cnt, J, lane);
         }
@@ -482,7 +663,8 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                 // others' bounds are then stale and they reload them)
                 grid_release(ctl, word, s_fresh | (solo ? kReloadFlag : 0ull));
             } else {
-                close_round(jobs, njobs, ubeg, ctl);
+                if (adm) close_round_admit(jobs, ubeg, ctl, adm);
+                else close_round(jobs, njobs, ubeg, ctl);
                 grid_release(ctl, word, 0);
             }
         } else if (!kMulti && threadIdx.x == 0) {
@@ -502,12 +684,11 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
     }
 }
 
-// Set up job j for a run from the identity: the table must already be cleared.
-__global__ void init_jobs_kernel(JobDev* jobs, int njobs, int only_fresh) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= njobs) return;
-    JobDev& J = jobs[j];
-    if (only_fresh && J.status != kFresh) return;
+}  // namespace
+
+// Set up one job for a run from the identity (or its start state): its visited set must already
+// be cleared.
+__device__ void init_job(JobDev& J) {
     uint64_t id = 0;
     for (int i = 0; i < J.n; ++i) id |= (uint64_t)i << (4 * i);
     if (J.use_start) id = J.start_key;      // a central state: the growth of its orbit
@@ -528,6 +709,16 @@ __global__ void init_jobs_kernel(JobDev* jobs, int njobs, int only_fresh) {
     if (J.max_radius == 0) J.status = kTruncRadius;
 }
 
+namespace {
+
+__global__ void init_jobs_kernel(JobDev* jobs, int njobs, int only_fresh) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= njobs) return;
+    JobDev& J = jobs[j];
+    if (only_fresh && J.status != kFresh) return;
+    init_job(J);
+}
+
 // Work layout of the first round (after init, or after the host resized a job's buffers):
 // one warp unit per 32 frontier states of every running job.
 __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl) {
@@ -545,6 +736,12 @@ __global__ void init_units_kernel(JobDev* jobs, int njobs, unsigned long long* u
     ctl->bar_word = 0;
     for (int g = 0; g < kBarGroups; ++g) ctl->group[g].count = 0;   // the barrier counters only grow
     ctl->err = 0;
+}
+
+// First admission of a batch launch (one block): admit the first jobs and lay out their work.
+__global__ void __launch_bounds__(kGrowBlock) admit_first_kernel(JobDev* jobs, unsigned long long* ubeg,
+                                                                 Ctl* ctl, const AdmitDev* adm) {
+    close_round_admit(jobs, ubeg, ctl, adm);
 }
 
 // Re-insert keys[0, count) of one job into its (cleared) table; used after the key array
@@ -615,7 +812,7 @@ __global__ void finish_insert_count_kernel(unsigned long long* count, const int*
 int hash_grow_block() { return kGrowBlock; }
 
 namespace {
-using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t);
+using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t, const AdmitDev*);
 // Kernel variants: `ilp` generators per thread (1..4); +8 selects whole-sector table probing,
 // +16 the rank bitmap; multi = launches of several jobs.
 template <bool M>
@@ -640,16 +837,16 @@ GrowFn grow_fn(int variant, bool multi) { return multi ? grow_fn_t<true>(variant
 
 // The single-job rank-bitmap kernel with one generator in flight per thread (the default for
 // S_n, n <= 14) is also compiled per n, so its rank arithmetic unrolls with constants.
-template <int... Ns>
+template <int kILP, int... Ns>
 GrowFn grow_fn_bitmap_n(int n, std::integer_sequence<int, Ns...>) {
     GrowFn f = nullptr;
-    (void)((n == Ns + 2 ? (f = hash_grow_kernel<1, 2, false, Ns + 2>, 0) : 0) + ...);
+    (void)((n == Ns + 2 ? (f = hash_grow_kernel<kILP, 2, false, Ns + 2>, 0) : 0) + ...);
     return f;
 }
 
 GrowFn grow_fn(int variant, bool multi, int n) {
     if (variant == 17 && !multi && n >= 2 && n <= 14)
-        return grow_fn_bitmap_n(n, std::make_integer_sequence<int, 13>{});
+        return grow_fn_bitmap_n<1>(n, std::make_integer_sequence<int, 13>{});
     return grow_fn(variant, multi);
 }
 }  // namespace
@@ -678,9 +875,16 @@ cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d
     return cudaGetLastError();
 }
 
+cudaError_t launch_admit_first(JobDev* d_jobs, unsigned long long* d_ubeg, Ctl* d_ctl,
+                               const AdmitDev* d_adm, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    admit_first_kernel<<<1, kGrowBlock, 0, st>>>(d_jobs, d_ubeg, d_ctl, d_adm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              int grid, int max_rounds, uint64_t timeout_ns, int ilp, cudaStream_t st,
-                             int n) {
+                             int n, const AdmitDev* d_adm) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -692,8 +896,8 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, njobs > 1, n), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
-                              timeout_ns);
+    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, njobs > 1 || d_adm != nullptr, n), d_jobs, njobs, d_ubeg,
+                              d_ctl, max_rounds, timeout_ns, d_adm);
 }
 
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/cg_growth.h"
+#include "cg_device.cuh"
 #include "cg_internal.h"
 #include "cg_kernels.h"
 #include "group_order.h"
@@ -140,6 +141,51 @@ bool make_gensm_checked(const uint8_t* g, int n, int w, GenSM& G) {
     return true;
 }
 
+// The same forms over two-word keys (WideGen): shift-and-mask over 128 bits with at most
+// kMaxWideTerms terms, else the reversal of one contiguous range (widths 1, 2, 4, whose
+// elements tile the 128 bits).  Returns false if neither fits.
+bool make_widegen_checked(const uint8_t* g, int n, int w, cg::WideGen& G) {
+    std::memset(&G, 0, sizeof(G));
+    G.width = (uint8_t)w;
+    bool fits = true;
+    for (int i = 0; i < n && fits; ++i) {
+        const unsigned rot = (unsigned)(((w * (i - (int)g[i])) % 128 + 128) & 127);
+        uint32_t t = 0;
+        while (t < G.nterms && G.rot[t] != rot) ++t;
+        if (t == G.nterms) {
+            if (G.nterms == (uint32_t)cg::kMaxWideTerms) { fits = false; break; }
+            G.rot[t] = (uint8_t)rot;
+            G.nterms++;
+        }
+        for (int b = 0; b < w; ++b) {
+            const int bit = w * i + b;
+            if (bit < 64) G.mlo[t] |= 1ull << bit;
+            else G.mhi[t] |= 1ull << (bit - 64);
+        }
+    }
+    if (fits) return true;
+    if (w != 1 && w != 2 && w != 4) return false;
+    int a = -1, b = -1;
+    for (int i = 0; i < n; ++i)
+        if (g[i] != i) {
+            if (a < 0) a = i;
+            b = i;
+        }
+    bool reversal = a >= 0 && b > a;
+    for (int i = a; reversal && i <= b; ++i) reversal = g[i] == a + b - i;
+    if (!reversal) return false;
+    std::memset(&G, 0, sizeof(G));
+    G.width = (uint8_t)w;
+    G.kind = 1;
+    const int elems = 128 / w;   // after the bit reversal element e sits at elems - 1 - e
+    G.rev_shift = (int16_t)(w * (elems - 1 - a - b));
+    for (int bit = w * a; bit < w * (b + 1); ++bit) {
+        if (bit < 64) G.mlo[0] |= 1ull << bit;
+        else G.mhi[0] |= 1ull << (bit - 64);
+    }
+    return true;
+}
+
 GenSM make_gensm(const uint8_t* g, int n, int w = 4) {
     GenSM G;
     make_gensm_checked(g, n, w, G);
@@ -172,6 +218,21 @@ std::vector<GenSM> make_gensms(const std::vector<std::vector<uint8_t>>& rows, in
     return out;
 }
 
+// Two-word forms of distinct rows with the inverse tags (as make_gensms); false if a row fits
+// neither form.
+bool make_widegens(const std::vector<std::vector<uint8_t>>& rows, int n, int w, std::vector<cg::WideGen>& out) {
+    out.assign(rows.size(), cg::WideGen{});
+    for (size_t j = 0; j < rows.size(); ++j)
+        if (!make_widegen_checked(rows[j].data(), n, w, out[j])) return false;
+    for (size_t j = 0; j < rows.size(); ++j) {
+        std::vector<uint8_t> inv(n);
+        for (int i = 0; i < n; ++i) inv[rows[j][i]] = (uint8_t)i;
+        for (size_t m = 0; m < rows.size() && m < 15; ++m)
+            if (rows[m] == inv) { out[j].inv_tag = (uint32_t)(m + 1); break; }
+    }
+    return true;
+}
+
 bool closed_under_inverse(const std::vector<std::vector<uint8_t>>& rows, int n) {
     std::set<std::vector<uint8_t>> s(rows.begin(), rows.end());
     for (auto& r : rows) {
@@ -188,6 +249,8 @@ int validate(int n, int k, const uint8_t* gens, int max_n = cg::kMaxN) {
         if (!is_perm_row(gens + (size_t)j * n, n)) return CG_EINVAL;
     return CG_OK;
 }
+
+size_t al_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 uint64_t next_pow2(uint64_t x) {
     uint64_t p = 1;
@@ -317,7 +380,11 @@ struct cg_growth {
     int mode = -1;                               // visited set chosen at the first run
     std::vector<std::vector<uint8_t>> rows;      // the distinct non-identity generators
     int width = 4;                               // bits per element of the packed keys
+    bool wide = false;                           // n * width > 64: two-word keys (wide_path.cu)
+    std::vector<cg::WideGen> wgsm;
+    cg::Key128 wstart{0, 0};
     bool use_start = false;                      // grow from a central state instead of e
+    bool start_constant = false;                 // every value of the start vector is the same
     uint64_t start_key = 0;
     bool start_is_perm = true;                   // the start vector has distinct entries
     uint64_t states_bound = 1;                   // states the growth can reach (orbit bound)
@@ -345,6 +412,15 @@ struct cg_growth {
     uint64_t* last_layer_ptr = nullptr;   // device pointer of the last reported layer
     uint64_t last_layer_n = 0;
     std::vector<uint64_t> sort_layers;
+
+    // two-word keys: generators, descriptor, states, visited table of 16-byte slots
+    cg::WideGen* d_wgens = nullptr;
+    cg::WideDev* d_wjob = nullptr;
+    cg::Key128* d_wkeys = nullptr;
+    uint64_t wkeys_cap = 0;
+    cg::Key128* d_wtable = nullptr;
+    uint64_t wtable_slots = 0;
+    cg::WideDev host_wide{};
 
     // sweep strategy: visited bitmap, three layer bitmaps with block bits and block lists
     SweepDev* d_sweep = nullptr;
@@ -374,6 +450,12 @@ struct cg_growth {
         d_sweep = nullptr;
         d_sw = nullptr;
         sw_bytes = 0;
+        dev_free(d_wgens, st);
+        dev_free(d_wjob, st);
+        dev_free(d_wkeys, st);
+        dev_free(d_wtable, st);
+        d_wgens = nullptr; d_wjob = nullptr; d_wkeys = nullptr; d_wtable = nullptr;
+        wkeys_cap = wtable_slots = 0;
         release_sort(st);
         have_last = false;                 // the last layer lived in the freed buffers
         last_layer_ptr = nullptr;
@@ -481,6 +563,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
                       ? cg::kVisitBitmap : cg::kVisitHash;
     }
     const bool bitmap = h->mode == cg::kVisitBitmap;
+    const int ilp = (h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k, bitmap)) + (bitmap ? 16 : 0);
     const uint64_t avail = mem > (1 << 20) ? mem - (1 << 20) : mem;
     const uint64_t bm_bytes = bitmap ? bitmap_words(h->n) * 4 : 0;
     const uint64_t max_cap = std::min<uint64_t>(
@@ -495,7 +578,6 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         rc = resize_state(h, std::max<uint64_t>(start, 1), 0, st);
         if (rc) return rc;
     }
-    const int ilp = (h->ilp_override > 0 ? h->ilp_override : default_ilp(h->k, bitmap)) + (bitmap ? 16 : 0);
     const int grid_max = grow_grid(h->device, ilp);
     if (grid_max <= 0) return CG_ECUDA;
     // Small groups finish faster with fewer blocks at each barrier.
@@ -569,6 +651,146 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     *final_status = J.status;
     h->last_layer_ptr = h->d_keys + J.lo;
     h->last_layer_n = J.hi - J.lo;
+    return CG_OK;
+}
+
+// ---- two-word keys ---------------------------------------------------------------------------
+// Vectors of more than 64 bits (wide_path.cu): one persistent launch; when the states or the
+// visited table run out the host grows both x4 (within mem_cap), re-inserts the stored states
+// and relaunches from the last complete layer, as run_hash does.
+
+// (Re)allocate states and table for `cap` states keeping the first `keep` states.
+int resize_wide(cg_growth* h, uint64_t cap, uint64_t keep, cudaStream_t st) {
+    auto* keys = (cg::Key128*)dev_alloc(cap * 16, st);
+    const uint64_t slots = table_slots_for(cap);
+    auto* table = (cg::Key128*)dev_alloc(slots * 16, st);
+    if (!keys || !table) { dev_free(keys, st); dev_free(table, st); return CG_ENOMEM; }
+    if (keep > 0) {
+        cudaError_t e = cudaMemcpyAsync(keys, h->d_wkeys, keep * 16, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { dev_free(keys, st); dev_free(table, st); return cuda_rc(e); }
+    }
+    dev_free(h->d_wkeys, st);
+    dev_free(h->d_wtable, st);
+    h->d_wkeys = keys;
+    h->d_wtable = table;
+    h->wkeys_cap = cap;
+    h->wtable_slots = slots;
+    return CG_OK;
+}
+
+int run_wide(cg_growth* h, cudaStream_t st, int* final_status) {
+    if (h->strategy != CG_STRATEGY_AUTO && h->strategy != CG_STRATEGY_HASH) return CG_EINVAL;
+    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
+    const uint64_t avail = mem > (1 << 20) ? mem - (1 << 20) : mem;
+    // 16 bytes a state plus 32 bytes of table (load <= 0.5), rounded to a power of two
+    uint64_t max_cap = 0;
+    for (int p = 10; p <= 40; ++p) {
+        const uint64_t slots = 1ull << p;
+        if (slots * 16 >= avail) break;
+        max_cap = std::max(max_cap, std::min<uint64_t>((uint64_t)(slots * kMaxLoad) - 1, (avail - slots * 16) / 16));
+    }
+    max_cap = std::min(max_cap, h->states_bound);
+    if (max_cap < 1) return CG_ENOMEM;
+    int rc = ensure_small_buffers(h, st);
+    if (rc) return rc;
+    if (!h->d_wgens) {
+        h->d_wgens = (cg::WideGen*)dev_alloc(sizeof(cg::WideGen) * std::max(1, h->k), st);
+        h->d_wjob = (cg::WideDev*)dev_alloc(sizeof(cg::WideDev), st);
+        if (!h->d_wgens || !h->d_wjob) return CG_ENOMEM;
+        cudaError_t e = cudaMemcpyAsync(h->d_wgens, h->wgsm.data(), sizeof(cg::WideGen) * h->k,
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_rc(e);
+        h->stats.h2d_bytes += sizeof(cg::WideGen) * h->k;
+    }
+    if (!h->d_wkeys) {
+        uint64_t start = std::min<uint64_t>(max_cap, 1ull << 22);
+        if (h->states_bound <= max_cap && h->states_bound * 48 <= std::min<uint64_t>(mem, kExactAllocLimit))
+            start = h->states_bound;
+        if ((rc = resize_wide(h, std::max<uint64_t>(start, 1), 0, st))) return rc;
+    }
+    const int tagged = h->n * h->width <= 124 ? 1 : 0;
+    auto fill = [&](cg::WideDev& D) {
+        D.keys = h->d_wkeys;
+        D.keys_cap = h->wkeys_cap;
+        D.table = h->d_wtable;
+        D.table_mask = h->wtable_slots - 1;
+        D.gens = h->d_wgens;
+        D.layer_sizes = h->d_layers;
+        D.stop_above = h->stop_above;
+        D.start = h->wstart;
+        D.k = h->k;
+        D.n = h->n;
+        D.layers_cap = cg::kMaxLayers;
+        D.max_radius = h->max_radius;
+        D.tagged = tagged;
+    };
+    cg::WideDev D;
+    std::memset(&D, 0, sizeof(D));
+    fill(D);
+    cudaError_t e = cudaMemsetAsync(h->d_wtable, 0xFF, h->wtable_slots * 16, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_wjob, &D, sizeof(D), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) e = cg::launch_wide_init(h->d_wjob, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    h->stats.launches += 1;
+    h->stats.h2d_bytes += sizeof(D);
+    if (!h->ev0) {
+        if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
+    }
+    const int grid_max = cg::wide_max_grid(h->device);
+    if (grid_max <= 0) return CG_ECUDA;
+    int grid = (int)std::min<uint64_t>((uint64_t)grid_max, h->states_bound / 512 + 1);
+    if (h->grid_override > 0) grid = std::min(grid_max, h->grid_override);
+    for (;;) {
+        if ((e = cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cg::launch_wide_grow(h->d_wjob, h->d_ctl, grid, cg::kMaxLayers + 1, kTimeoutNs, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.launches += 1;
+        Ctl ctl;
+        if ((e = cudaMemcpyAsync(&D, h->d_wjob, sizeof(D), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaMemcpyAsync(&ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.d2h_bytes += sizeof(D) + sizeof(ctl);
+        h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
+        h->stats.rounds += ctl.rounds;
+        if (ctl.err) return ctl.err;
+        if (D.status != cg::kNeedMem) break;
+        if (h->wkeys_cap >= max_cap) break;   // cannot grow: truncated by mem_cap
+        const uint64_t keep = D.hi;
+        const uint64_t newcap = std::min<uint64_t>(max_cap, std::max<uint64_t>(h->wkeys_cap * 4, keep + 1));
+        if ((rc = resize_wide(h, newcap, keep, st))) return rc;
+        if ((e = cudaMemsetAsync(h->d_wtable, 0xFF, h->wtable_slots * 16, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cg::launch_wide_rebuild(h->d_wkeys, keep, h->d_wtable, h->wtable_slots - 1, tagged,
+                                         &h->d_ctl->err, grid_max, st)) != cudaSuccess)
+            return cuda_rc(e);
+        fill(D);
+        D.tail = D.hi;
+        D.overflow = 0;
+        D.status = cg::kRunning;
+        if ((e = cudaMemcpyAsync(h->d_wjob, &D, sizeof(D), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_rc(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+        int derr = 0;
+        if ((e = cudaMemcpy(&derr, &h->d_ctl->err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_rc(e);
+        if (derr) return derr;
+        h->stats.launches += 1;
+        h->stats.h2d_bytes += sizeof(D);
+    }
+    h->stats.state_capacity = h->wkeys_cap;
+    h->stats.table_slots = h->wtable_slots;
+    h->stats.strategy_used = CG_STRATEGY_HASH;
+    h->stats.probe_variant = 1;
+    h->host_wide = D;
+    std::memset(&h->host_job, 0, sizeof(h->host_job));
+    h->host_job.radius = D.radius;
+    h->host_job.status = D.status;
+    *final_status = D.status;
     return CG_OK;
 }
 
@@ -905,21 +1127,29 @@ int cg_growth_create(int n, int k, const uint8_t* gens, int inverse_closed, int 
                      uint64_t mem_cap, cg_growth_t* out) {
     if (out == nullptr) return CG_EINVAL;
     *out = nullptr;
-    // n > 16 only grows from a start vector of narrow values (cg_growth_set_start)
-    int rc = validate(n, k, gens, cg::kMaxElems);
+    // n > 16: from the identity with 5-bit elements (n <= 25, two-word keys), or from a start
+    // vector of narrow values (cg_growth_set_start), up to 128 elements
+    int rc = validate(n, k, gens, cg::kMaxWideElems);
     if (rc) return rc;
     auto rows = clean_rows(n, k, gens);
     if (inverse_closed && !closed_under_inverse(rows, n)) return CG_ENOTCLOSED;
-    for (auto& r : rows) {   // with one bit per element: more than 16 offsets need a reversal
-        GenSM G;
-        if (!make_gensm_checked(r.data(), n, 1, G)) return CG_EINVAL;
-    }
     cg_growth* h = new (std::nothrow) cg_growth();
     if (!h) return CG_ENOMEM;
     h->n = n;
     h->k = (int)rows.size();
     h->rows = rows;
-    h->gsm = make_gensms(rows, n);
+    if (n <= cg::kMaxN) {
+        h->gsm = make_gensms(rows, n);
+    } else {
+        h->width = 5;
+        h->wide = true;
+        if (n > 25 || !make_widegens(rows, n, 5, h->wgsm)) h->wgsm.clear();   // no growth from e
+        for (int i = 0; i < n && n <= 25; ++i) {
+            const int bit = 5 * i;
+            if (bit < 64) h->wstart.lo |= (uint64_t)i << bit;
+            if (bit + 5 > 64) h->wstart.hi |= bit >= 64 ? (uint64_t)i << (bit - 64) : (uint64_t)i >> (64 - bit);
+        }
+    }
     h->inverse_closed = inverse_closed ? 1 : 0;
     h->max_radius = max_radius < 0 ? -1 : max_radius;
     h->mem_cap = mem_cap ? mem_cap : kDefaultMemCap;
@@ -942,12 +1172,21 @@ int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
             maxv = std::max(maxv, (int)start[i]);
         }
     // Permutations keep 4 bits per element (the rank-indexed strategies read them); other
-    // vectors take the narrowest width that holds their values: binary vectors 1 bit.
+    // vectors take the narrowest width that holds their values: binary vectors 1 bit.  Keys of
+    // more than 64 bits, or generators that the one-word forms cannot express, take two words.
     bool distinct = true;
     for (int v = 0; v < 16; ++v) distinct &= count[v] <= 1;
     const bool is_perm = start && distinct && maxv < h->n;
     const int w = is_perm ? 4 : maxv <= 1 ? 1 : maxv <= 3 ? 2 : 4;
-    if (start && h->n * w > 64) return CG_EINVAL;
+    if (start && h->n * w > 128) return CG_EINVAL;
+    std::vector<GenSM> narrow;
+    bool use_narrow = start && h->n * w <= 64;
+    for (size_t j = 0; use_narrow && j < h->rows.size(); ++j) {
+        GenSM G;
+        use_narrow = make_gensm_checked(h->rows[j].data(), h->n, w, G);
+    }
+    std::vector<cg::WideGen> wg;
+    if (start && !use_narrow && !make_widegens(h->rows, h->n, w, wg)) return CG_EINVAL;
     if (h->device >= 0) {                 // buffers were sized for the previous start
         h->release(nullptr);
         cudaStreamSynchronize(nullptr);
@@ -957,13 +1196,32 @@ int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
         h->use_start = false;
         h->start_key = 0;
         h->start_is_perm = true;
-        h->width = 4;
-        h->gsm = make_gensms(h->rows, h->n, 4);
+        h->width = h->n <= cg::kMaxN ? 4 : 5;
+        h->wide = h->n > cg::kMaxN;
+        if (!h->wide) {
+            h->gsm = make_gensms(h->rows, h->n, 4);
+        } else if (h->n > 25 || !make_widegens(h->rows, h->n, 5, h->wgsm)) {
+            h->wgsm.clear();
+        }
+        if (h->wide) {
+            h->wstart = cg::Key128{0, 0};
+            for (int i = 0; i < h->n && h->n <= 25; ++i) {
+                const int bit = 5 * i;
+                if (bit < 64) h->wstart.lo |= (uint64_t)i << bit;
+                if (bit + 5 > 64) h->wstart.hi |= bit >= 64 ? (uint64_t)i << (bit - 64) : (uint64_t)i >> (64 - bit);
+            }
+        }
         h->states_bound = h->order;
         return CG_OK;
     }
     uint64_t key = 0;
-    for (int i = 0; i < h->n; ++i) key |= (uint64_t)start[i] << (w * i);
+    cg::Key128 wkey{0, 0};
+    for (int i = 0; i < h->n; ++i) {
+        const int bit = w * i;
+        if (bit < 64) wkey.lo |= (uint64_t)start[i] << bit;
+        else wkey.hi |= (uint64_t)start[i] << (bit - 64);
+        if (bit < 64) key |= (uint64_t)start[i] << bit;
+    }
     // The orbit of the start vector has at most as many states as the group, and at most as
     // many as the distinct rearrangements of the vector (a multinomial coefficient), computed as
     // a product of binomials, saturating at 2^64 - 1.
@@ -978,9 +1236,13 @@ int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
     }
     h->use_start = true;
     h->start_key = key;
+    h->start_constant = count[start[0]] == h->n;
     h->start_is_perm = is_perm;
     h->width = w;
-    h->gsm = make_gensms(h->rows, h->n, w);
+    h->wide = !use_narrow;
+    if (use_narrow) h->gsm = make_gensms(h->rows, h->n, w);
+    else h->wgsm = wg;
+    h->wstart = wkey;
     h->states_bound = std::min(h->order, rearr);
     return CG_OK;
 }
@@ -1028,12 +1290,14 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
     cudaStream_t st = (cudaStream_t)cuda_stream;
     h->have_last = false;
     std::memset(&h->stats, 0, sizeof(h->stats));
-    if (!h->use_start && h->n > cg::kMaxN) return CG_EINVAL;   // the identity needs 4-bit elements
-    if (h->k == 0 || h->max_radius == 0) {  // trivial group or radius 0: only the identity
+    // from the identity beyond 16 elements: 5-bit elements in two words, n <= 25
+    if (!h->use_start && h->wide && h->wgsm.empty()) return CG_EINVAL;
+    // trivial group, radius 0, or a constant start vector (every permutation fixes it): one state
+    if (h->k == 0 || h->max_radius == 0 || (h->use_start && h->start_constant)) {
         *num_layers_out = 1;
         if (cap < 1) return CG_EINVAL;
         layer_sizes_out[0] = 1;
-        return h->k == 0 ? CG_OK : CG_TRUNC_RADIUS;
+        return (h->k == 0 || h->max_radius != 0) ? CG_OK : CG_TRUNC_RADIUS;
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1041,6 +1305,20 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
     if (h->device >= 0 && h->device != dev) return CG_EINVAL;
     h->device = dev;
     int status = 0;
+    if (h->wide) {
+        int rc = run_wide(h, st, &status);
+        if (rc) return rc;
+        h->last_is_sweep = false;
+        const int layers = h->host_job.radius + 1;
+        *num_layers_out = layers;
+        if (cap < layers) return CG_EINVAL;
+        e = cudaMemcpyAsync(layer_sizes_out, h->d_layers, sizeof(uint64_t) * layers, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_rc(e);
+        h->stats.d2h_bytes += sizeof(uint64_t) * layers;
+        h->have_last = true;
+        return status_to_rc(status);
+    }
     const bool use_sort = h->strategy == CG_STRATEGY_SORT;
     const bool use_sweep = h->strategy == CG_STRATEGY_SWEEP ||
                            (h->strategy == CG_STRATEGY_AUTO && sweep_preferred(h));
@@ -1071,6 +1349,17 @@ int cg_growth_run(cg_growth_t h, void* cuda_stream, uint64_t* layer_sizes_out, i
 
 int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64_t* count_out) {
     if (!h || !count_out || !h->have_last) return CG_EINVAL;
+    if (h->wide) {
+        // two words a state (low, high), the parent-edge tags of stored states stripped
+        const cg::WideDev& D = h->host_wide;
+        const uint64_t cnt = D.hi - D.lo;
+        *count_out = cnt;
+        if (cap < cnt || (!keys_out && cnt > 0)) return CG_EINVAL;
+        cudaError_t e = cudaMemcpy(keys_out, h->d_wkeys + D.lo, cnt * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && D.tagged)
+            for (uint64_t i = 0; i < cnt; ++i) keys_out[2 * i + 1] &= (1ull << 60) - 1;
+        return cuda_rc(e);
+    }
     if (h->last_is_sweep) {
         // unrank the last layer's bitmap (layer R lives in F[R % 3], its blocks in L[R % 3])
         const SweepDev& D = h->host_sweep;
@@ -1110,6 +1399,8 @@ int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64
 uint64_t cg_growth_group_order(cg_growth_t h) { return h ? h->order : 0; }
 
 int cg_growth_key_width(cg_growth_t h) { return h ? h->width : 0; }
+
+int cg_growth_key_words(cg_growth_t h) { return h ? (h->wide ? 2 : 1) : 0; }
 
 const char* cg_last_error_detail(void) {
     if (g_last_cuda_error == cudaSuccess) return "";
@@ -1230,6 +1521,44 @@ int cg_perm_unrank(int n, const uint64_t* ranks, uint64_t count, uint64_t* keys,
     return cuda_rc(cg::launch_pos_unrank(ranks, count, n, keys, sms * 8, (cudaStream_t)cuda_stream));
 }
 
+int cg_shard_owner(uint64_t key, int P) {
+    if (P < 1) return CG_EINVAL;
+    return (int)(cg::mix64(key) % (uint64_t)P);
+}
+
+int cg_shard_expand(int n, int k, const uint8_t* gens, const uint64_t* frontier, uint64_t F, int P,
+                    uint64_t* out, uint64_t cap, uint64_t* counts_out, void* cuda_stream) {
+    int rc = validate(n, k, gens);
+    if (rc) return rc;
+    if (P < 1 || P > 4096 || !counts_out || (F > 0 && (!frontier || !out))) return CG_EINVAL;
+    if (cap < (uint64_t)k * F) return CG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::vector<GenSM> g;
+    for (int j = 0; j < k; ++j) g.push_back(make_gensm(gens + (size_t)j * n, n));
+    const size_t gbytes = al_up(sizeof(GenSM) * k);
+    char* d = (char*)dev_alloc(gbytes + 2 * sizeof(unsigned long long) * P + 256, st);
+    if (!d) return CG_ENOMEM;
+    GenSM* d_gens = reinterpret_cast<GenSM*>(d);
+    unsigned long long* d_counts = reinterpret_cast<unsigned long long*>(d + gbytes);
+    unsigned long long* d_cursor = d_counts + P;
+    int* d_err = reinterpret_cast<int*>(d_cursor + P);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_gens, g.data(), sizeof(GenSM) * k, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cg::launch_owner_partition(d_gens, k, frontier, F, P, d_counts, d_cursor, out, cap, d_err,
+                                       std::max(sms, 1) * 8, st);
+    int derr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts_out, d_counts, sizeof(uint64_t) * P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // g and derr live on the host stack
+    dev_free(d, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    return derr ? derr : CG_OK;
+}
+
 int cg_hash_clear(uint64_t* table, uint64_t slots, void* cuda_stream) {
     if (!table && slots) return CG_EINVAL;
     return cuda_rc(cudaMemsetAsync(table, 0xFF, slots * 8, (cudaStream_t)cuda_stream));
@@ -1270,9 +1599,15 @@ struct cg_batch {
     };
     struct Wave {
         std::vector<int> ids;
+        bool admit = false;        // one launch admitting its jobs by the L2 window (AdmitDev)
         char* base = nullptr;      // resident plans: the wave's device buffer
         uint64_t bytes = 0;
         uint64_t o_gens = 0, o_jobs = 0, o_ubeg = 0, o_ctl = 0, o_lay = 0, o_keys = 0, o_tab = 0;
+        uint64_t o_adm = 0, o_act = 0, o_vis = 0;
+        std::vector<uint64_t> vis;               // admit: visited bytes counted per job
+        uint64_t window = 0;
+        int max_active = 0;
+        int unit_mult = 1;
         std::vector<uint64_t> slots;             // visited-set 8-byte slots per job
         std::vector<std::pair<uint64_t, uint64_t>> clear_runs[2];  // (offset, bytes): 0 -> 0x00, 1 -> 0xFF
         std::vector<GenSM> hg;
@@ -1285,7 +1620,9 @@ struct cg_batch {
     int ilp_override = 0;          // CG_OPT_ILP
     int grid_override = 0;         // CG_OPT_GRID
     int visited = 0;               // CG_OPT_BATCH_VISITED
-    int use_graph = 0;             // CG_OPT_GRAPH (-1 after a failed capture)
+    int use_graph = 1;             // CG_OPT_GRAPH (-1 after a failed capture)
+    int max_active = 0;            // CG_OPT_BATCH_ACTIVE (0: min(jobs, 2048))
+    int unit_mult = 4;             // CG_OPT_UNIT
     cg_growth_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -1346,6 +1683,12 @@ void layout_wave(cg_batch* b, cg_batch::Wave& w, int lcap) {
     w.o_keys = al256(w.o_lay + (uint64_t)nj * lcap * 8);
     w.o_tab = al256(w.o_keys + nkeys * 8);
     w.bytes = al256(w.o_tab + nslots * 8);
+    if (w.admit) {
+        w.o_adm = w.bytes;
+        w.o_act = al256(w.o_adm + sizeof(cg::AdmitDev));
+        w.o_vis = al256(w.o_act + 2ull * (uint64_t)w.max_active * sizeof(int));
+        w.bytes = al256(w.o_vis + (uint64_t)nj * 8);
+    }
     // visited sets: bitmaps start all-zero, hash tables all-ones; runs of one kind, one memset each
     for (auto& r : w.clear_runs) r.clear();
     for (int i = 0; i < nj;) {
@@ -1396,7 +1739,20 @@ cudaError_t bind_wave(cg_batch::Wave& w, char* base, cudaStream_t st) {
                                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + w.o_jobs, hj.data(), hj.size() * sizeof(JobDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // hj is a local copy
+    cg::AdmitDev A{};
+    if (w.admit) {
+        A.act[0] = reinterpret_cast<int*>(base + w.o_act);
+        A.act[1] = A.act[0] + w.max_active;
+        A.vis = reinterpret_cast<const uint64_t*>(base + w.o_vis);
+        A.window = w.window;
+        A.max_active = w.max_active;
+        A.njobs = (int)w.ids.size();
+        A.unit_mult = w.unit_mult;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(base + w.o_adm, &A, sizeof(A), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + w.o_vis, w.vis.data(), w.vis.size() * 8, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // hj, A are local copies
     return e;
 }
 
@@ -1418,9 +1774,18 @@ cudaError_t enqueue_wave(cg_batch* b, cg_batch::Wave& w, char* base, char* hout,
     unsigned long long* d_ubeg = reinterpret_cast<unsigned long long*>(base + w.o_ubeg);
     Ctl* d_ctl = reinterpret_cast<Ctl*>(base + w.o_ctl);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st);
-    if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
-    if (e == cudaSuccess)
-        e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, b->grid, lcap + 1, kTimeoutNs, b->ilp, st);
+    if (w.admit) {
+        // one launch for the whole batch: jobs are admitted (and set up) as the window allows
+        const cg::AdmitDev* d_adm = reinterpret_cast<const cg::AdmitDev*>(base + w.o_adm);
+        if (e == cudaSuccess) e = cg::launch_admit_first(d_jobs, d_ubeg, d_ctl, d_adm, st);
+        if (e == cudaSuccess)
+            e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, b->grid, 1 << 30, kTimeoutNs, b->ilp, st,
+                                     0, d_adm);
+    } else {
+        if (e == cudaSuccess) e = cg::launch_init_jobs(d_jobs, nj, d_ubeg, d_ctl, st);
+        if (e == cudaSuccess)
+            e = cg::launch_hash_grow(d_jobs, nj, d_ubeg, d_ctl, b->grid, lcap + 1, kTimeoutNs, b->ilp, st);
+    }
     const uint64_t o1 = al256(nj * sizeof(JobDev)), o2 = o1 + al256(sizeof(Ctl));
     if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_jobs, nj * sizeof(JobDev), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hout + o1, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
@@ -1487,35 +1852,64 @@ int plan_batch(cg_batch* b, int dev, int cap, cudaStream_t st) {
         }
         l2_cap = (uint64_t)l2 / 2;
     }
-    // Greedy waves in job order, each within the memory budget and with visited sets that
-    // together fit the L2 cap (a set larger than the cap misses L2 wherever it runs and does not
-    // count).  Jobs with no work (no generator, radius 0) are answered on the host.
+    // When every job's buffers fit the budget together, the batch is one launch that admits
+    // the jobs in order as the L2 window allows (AdmitDev).  Otherwise greedy waves in job
+    // order, each within the memory budget and with visited sets that together fit the L2 cap,
+    // allocated and run one after the other.  Either way a set larger than the cap misses L2
+    // wherever it runs and does not count.  Jobs with no work (no generator, radius 0) are
+    // answered on the host.
     const int lcap = cap + 1;
-    cg_batch::Wave cur;
-    uint64_t wave_bytes = 0, wave_vis = 0, total_bytes = 0;
-    auto close_wave = [&]() {
-        if (cur.ids.empty()) return;
-        layout_wave(b, cur, lcap);
-        total_bytes += cur.bytes;
-        b->waves.push_back(std::move(cur));
-        cur = cg_batch::Wave();
-        wave_bytes = wave_vis = 0;
-    };
+    std::vector<uint64_t> need_of(b->jobs.size(), 0), vis_of(b->jobs.size(), 0);
+    uint64_t all_need = 0;
+    int with_work = 0;
     for (int j = 0; j < (int)b->jobs.size(); ++j) {
         auto& J = b->jobs[j];
         if (J.k == 0 || J.max_radius == 0) continue;
         J.cap = std::max<uint64_t>(1, std::min<uint64_t>(J.order, per_job_max));
         const uint64_t set_bytes = J.mode == cg::kVisitBitmap ? bitmap_words(J.n) * 4
                                                                : table_slots_for(J.cap) * 8;
-        const uint64_t need = J.cap * 8 + set_bytes + sizeof(GenSM) * J.gsm.size() +
-                              sizeof(JobDev) + (uint64_t)lcap * 8 + 1024;
-        const uint64_t vis = set_bytes <= l2_cap ? set_bytes : 0;
-        if (!cur.ids.empty() && (wave_bytes + need > budget || wave_vis + vis > l2_cap)) close_wave();
-        cur.ids.push_back(j);
-        wave_bytes += need;
-        wave_vis += vis;
+        need_of[j] = J.cap * 8 + set_bytes + sizeof(GenSM) * J.gsm.size() + sizeof(JobDev) +
+                     (uint64_t)lcap * 8 + 1024;
+        vis_of[j] = set_bytes <= l2_cap ? set_bytes : 0;
+        all_need += need_of[j] + 16;
+        ++with_work;
     }
-    close_wave();
+    uint64_t total_bytes = 0;
+    if (with_work > 0 && all_need + (4ull << 20) <= budget) {
+        cg_batch::Wave w;
+        w.admit = true;
+        w.window = l2_cap;
+        w.max_active = b->max_active > 0 ? std::min(b->max_active, with_work) : std::min(with_work, 2048);
+        w.unit_mult = b->unit_mult;
+        for (int j = 0; j < (int)b->jobs.size(); ++j)
+            if (need_of[j]) {
+                w.ids.push_back(j);
+                w.vis.push_back(vis_of[j]);
+            }
+        layout_wave(b, w, lcap);
+        total_bytes = w.bytes;
+        b->waves.push_back(std::move(w));
+    } else {
+        cg_batch::Wave cur;
+        uint64_t wave_bytes = 0, wave_vis = 0;
+        auto close_wave = [&]() {
+            if (cur.ids.empty()) return;
+            layout_wave(b, cur, lcap);
+            total_bytes += cur.bytes;
+            b->waves.push_back(std::move(cur));
+            cur = cg_batch::Wave();
+            wave_bytes = wave_vis = 0;
+        };
+        for (int j = 0; j < (int)b->jobs.size(); ++j) {
+            if (!need_of[j]) continue;
+            if (!cur.ids.empty() && (wave_bytes + need_of[j] > budget || wave_vis + vis_of[j] > l2_cap))
+                close_wave();
+            cur.ids.push_back(j);
+            wave_bytes += need_of[j];
+            wave_vis += vis_of[j];
+        }
+        close_wave();
+    }
     // pinned host memory for every wave's results
     uint64_t hb = 0;
     for (auto& w : b->waves) {
@@ -1649,7 +2043,7 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
             if ((e = cudaGraphLaunch(b->gexec, b->gstream)) != cudaSuccess) return cuda_rc(e);
             if ((e = cudaEventRecord(b->ev1, b->gstream)) != cudaSuccess) return cuda_rc(e);
             if ((e = cudaStreamSynchronize(b->gstream)) != cudaSuccess) return cuda_rc(e);
-            b->stats.launches += 1;     // one graph: its kernels are counted below
+            // one graph launch: its kernels are counted below
         } else {
             if ((e = cudaEventRecord(b->ev0, st)) != cudaSuccess) return cuda_rc(e);
             if ((e = enqueue_resident_run(b, st)) != cudaSuccess) return cuda_rc(e);
@@ -1658,7 +2052,7 @@ int cg_batch_run(cg_batch_t b, void* cuda_stream, uint64_t* layer_sizes_out, int
         }
         b->stats.kernel_ms += elapsed_ms(b->ev0, b->ev1);
         for (auto& w : b->waves) {
-            b->stats.launches += 3;     // init_jobs + init_units + grow
+            b->stats.launches += w.admit ? 2 : 3;     // (admit_first | init_jobs + init_units) + grow
             b->stats.d2h_bytes += wave_result_bytes(w, lcap);
             int r = collect_wave(b, w, b->h_pinned + w.h_off, lcap, cap, layer_sizes_out,
                                  num_layers_out, status_out);
@@ -1712,6 +2106,14 @@ int cg_batch_set_option(cg_batch_t b, int option, int64_t value) {
             b->use_graph = value ? 1 : 0;
             b->drop_graph();
             return CG_OK;
+        case CG_OPT_BATCH_ACTIVE:
+            if (value < 0 || value > (1 << 20)) return CG_EINVAL;
+            b->max_active = (int)value;
+            break;
+        case CG_OPT_UNIT:
+            if (value != 1 && value != 2 && value != 4 && value != 8) return CG_EINVAL;
+            b->unit_mult = (int)value;
+            break;
         default:
             return CG_EINVAL;
     }
@@ -1768,6 +2170,39 @@ uint64_t predict_states(int k, uint64_t order, int max_radius, bool inverse_clos
         if (total >= order) return order;
     }
     return std::min(total, order);
+}
+
+// Device memory plan of one served job: the predicted states up to its radius cap (`want`),
+// and the states it may store within `share` bytes (`cap`) with the cheaper visited set -- a
+// hash table (8-byte key + 16 bytes of table per state at load 0.5) or, for n <= 14, the rank
+// bitmap (n!/8 bytes whatever the states).  A job whose prediction exceeds the share gets the
+// share and stops with CG_TRUNC_MEMCAP if it really needs more.
+struct SrvPlan {
+    uint64_t want = 1, cap = 1, bytes = 0, visited_words = 0;
+    int mode = cg::kVisitHash;
+};
+
+SrvPlan plan_server_job(int n, int k, uint64_t order, int max_radius, bool inverse_closed, uint64_t share) {
+    SrvPlan P;
+    P.want = std::max<uint64_t>(1, predict_states(std::max(k, 1), order, max_radius, inverse_closed));
+    uint64_t hcap = P.want;
+    if (bytes_for(hcap) > share) hcap = std::max<uint64_t>(1, max_cap_for_mem(share));
+    uint64_t bcap = 0;
+    const uint64_t bm_bytes = (n >= 2 && n <= 14) ? bitmap_words(n) * 4 : ~0ull;
+    if (bm_bytes < share) bcap = std::min<uint64_t>(P.want, (share - bm_bytes) / 8);
+    const uint64_t hbytes = hcap * 8 + table_slots_for(hcap) * 8;
+    const bool bitmap = bcap > hcap || (bcap == hcap && bcap > 0 && bcap * 8 + bm_bytes <= hbytes);
+    if (bitmap) {
+        P.mode = cg::kVisitBitmap;
+        P.cap = std::max<uint64_t>(bcap, 1);
+        P.visited_words = bm_bytes / 8;
+    } else {
+        P.mode = cg::kVisitHash;
+        P.cap = hcap;
+        P.visited_words = table_slots_for(hcap);
+    }
+    P.bytes = ((P.cap * 8 + 255) & ~255ull) + P.visited_words * 8;
+    return P;
 }
 
 }  // namespace
@@ -1891,7 +2326,7 @@ int cg_server_create(uint64_t mem_budget, int max_slots, uint64_t job_mem_cap, i
     cg_server* s = new (std::nothrow) cg_server();
     if (!s) return CG_ENOMEM;
     s->budget = mem_budget ? mem_budget : kDefaultMemCap;
-    s->job_cap_bytes = job_mem_cap ? job_mem_cap : (2ull << 30);
+    s->job_cap_bytes = job_mem_cap ? job_mem_cap : std::max<uint64_t>(s->budget / 64, 1ull << 20);
     s->max_slots = max_slots;
     s->rounds_per_step = rounds_per_step;
     s->slots.resize(max_slots);
@@ -1916,26 +2351,12 @@ int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inver
     std::vector<uint8_t> flat;
     for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
     J.order = rows.empty() ? 1 : cg::group_order(n, (int)rows.size(), flat.data());
-    // predicted memory: states up to the radius cap, within the per-job cap
-    const uint64_t want = std::max<uint64_t>(1, predict_states(std::max(J.k, 1), J.order, J.max_radius,
-                                                               inverse_closed != 0));
-    const bool bm_ok = n <= 12 && n >= 2;
-    const uint64_t bm_bytes = bm_ok ? bitmap_words(n) * 4 : ~0ull;
-    uint64_t cap = want;
-    uint64_t hash_bytes = cap * 8 + table_slots_for(cap) * 8;
-    if (hash_bytes > s->job_cap_bytes) {
-        cap = std::max<uint64_t>(1, max_cap_for_mem(s->job_cap_bytes));
-        hash_bytes = cap * 8 + table_slots_for(cap) * 8;
-    }
-    if (bm_ok && cap * 8 + bm_bytes <= hash_bytes) {
-        J.mode = cg::kVisitBitmap;
-        J.visited_words = bm_bytes / 8;
-    } else {
-        J.mode = cg::kVisitHash;
-        J.visited_words = table_slots_for(cap);
-    }
-    J.cap = cap;
-    J.bytes = ((cap * 8 + 255) & ~255ull) + J.visited_words * 8;
+    // predicted memory: states up to the radius cap, within the per-job share
+    const SrvPlan P = plan_server_job(n, J.k, J.order, J.max_radius, inverse_closed != 0, s->job_cap_bytes);
+    J.mode = P.mode;
+    J.visited_words = P.visited_words;
+    J.cap = P.cap;
+    J.bytes = P.bytes;
     if (J.k == 0 || J.max_radius == 0) {       // only the identity: done at once
         cg_server::Result R;
         R.layers = {1};
@@ -1946,6 +2367,25 @@ int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inver
         s->queue.push_back(std::move(J));
     }
     *job_id_out = s->next_id - 1;
+    return CG_OK;
+}
+
+int cg_server_predict(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
+                      uint64_t job_mem_cap, uint64_t* states_out, uint64_t* granted_out,
+                      uint64_t* bytes_out) {
+    int rc = validate(n, k, gens);
+    if (rc) return rc;
+    if (job_mem_cap == 0) return CG_EINVAL;
+    auto rows = clean_rows(n, k, gens);
+    if (inverse_closed && !closed_under_inverse(rows, n)) return CG_ENOTCLOSED;
+    std::vector<uint8_t> flat;
+    for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
+    const uint64_t order = rows.empty() ? 1 : cg::group_order(n, (int)rows.size(), flat.data());
+    const int rad = max_radius < 0 ? -1 : max_radius;
+    const SrvPlan P = plan_server_job(n, (int)rows.size(), order, rad, inverse_closed != 0, job_mem_cap);
+    if (states_out) *states_out = P.want;
+    if (granted_out) *granted_out = P.cap;
+    if (bytes_out) *bytes_out = P.bytes;
     return CG_OK;
 }
 

@@ -1,7 +1,8 @@
 """Autotuner for the launch settings of batched and single growths.
 
 The library's defaults are rules (kernel variant from the generator count, blocks from
-co-residency, launches ("waves") capped at half of L2, rank bitmap for dense groups of n <= 12).
+co-residency, jobs grown at once capped by half of L2 and at 2048, work units of 128 frontier
+states, rank bitmap for dense groups of n <= 12).
 The tuner times the actual workload under alternative settings and keeps the fastest, one knob at
 a time (coordinate descent from the defaults), and records the winner in a JSON table keyed by a
 signature of the workload and the device, so that later runs of the same kind of workload start
@@ -25,11 +26,13 @@ MiB = 1 << 20
 # Knobs and their candidate values, in the order they are tuned.  "grid" is in blocks per SM
 # (the library caps it at co-residency).
 BATCH_KNOBS = (
-    ("visited", ("auto", "hash")),
+    ("visited", ("auto", "hash", "bitmap")),
     ("ilp", (0, 1, 2, 3, 4)),
     ("grid_per_sm", (0, 4, 3, 2, 1)),
     ("wave_l2", (0, 16 * MiB, 32 * MiB, 96 * MiB, -1)),
-    ("graph", (False, True)),
+    ("max_active", (0, 256, 512, 2048)),
+    ("unit", (4, 1, 2, 8)),
+    ("graph", (True, False)),
 )
 
 GROWTH_KNOBS = (
@@ -121,6 +124,7 @@ def batch_options(settings: dict, sms: int) -> dict:
     """Batch.set_options arguments of a settings dict."""
     return {"visited": settings["visited"], "ilp": settings["ilp"],
             "grid": settings["grid_per_sm"] * sms, "wave_l2": settings["wave_l2"],
+            "max_active": settings.get("max_active", 0), "unit": settings.get("unit", 4),
             "graph": settings["graph"]}
 
 

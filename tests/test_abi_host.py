@@ -98,7 +98,7 @@ def _create(lib, n, gens, inv=0, maxr=-1):
 
 def test_create_validation(lib):
     assert _create(lib, 3, [[0, 0, 1]])[0] == lib.CG_EINVAL          # not a permutation
-    assert _create(lib, 65, [list(range(65))])[0] == lib.CG_EINVAL   # n > 64
+    assert _create(lib, 129, [list(range(129))])[0] == lib.CG_EINVAL   # n > 128
     assert _create(lib, 0, [[]])[0] == lib.CG_EINVAL
     assert _create(lib, 5, w.lx(5), inv=1)[0] == lib.CG_ENOTCLOSED
     rc, h = _create(lib, 5, w.lrx(5), inv=1)
@@ -127,17 +127,26 @@ def test_set_start_validation(lib):
     assert lib.cg_growth_set_start(h, ok.ctypes.data_as(u8)) == 0
     assert lib.cg_growth_set_start(h, None) == 0
     lib.cg_growth_destroy(h)
-    # n > 16: only from a start vector whose values fit n * width <= 64 bits
+    # n > 16: from the identity only up to n = 25 (5-bit elements in two words); longer vectors
+    # from a start vector whose values fit n * width <= 128 bits
     rc, h = _create(lib, 40, [list(range(1, 40)) + [0]], inv=0)
     assert rc == 0
     out = np.zeros(8, dtype=np.uint64)
     nl = ctypes.c_int(0)
     assert lib.cg_growth_run(h, None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 8,
                              ctypes.byref(nl)) == lib.CG_EINVAL          # identity of S_40
-    two_bit = np.array([3] + [0] * 39, dtype=np.uint8)                     # 80 bits: too wide
-    one_bit = np.array([1] * 20 + [0] * 20, dtype=np.uint8)                # 40 bits
-    assert lib.cg_growth_set_start(h, two_bit.ctypes.data_as(u8)) == lib.CG_EINVAL
+    four_bit = np.array([5] + [0] * 39, dtype=np.uint8)                    # 160 bits: too wide
+    two_bit = np.array([3] + [0] * 39, dtype=np.uint8)                     # 80 bits: two words
+    one_bit = np.array([1] * 20 + [0] * 20, dtype=np.uint8)                # 40 bits: one word
+    assert lib.cg_growth_set_start(h, four_bit.ctypes.data_as(u8)) == lib.CG_EINVAL
+    assert lib.cg_growth_set_start(h, two_bit.ctypes.data_as(u8)) == 0
+    assert lib.cg_growth_key_words(h) == 2 and lib.cg_growth_key_width(h) == 2
     assert lib.cg_growth_set_start(h, one_bit.ctypes.data_as(u8)) == 0
+    assert lib.cg_growth_key_words(h) == 1 and lib.cg_growth_key_width(h) == 1
+    lib.cg_growth_destroy(h)
+    # the identity of S_20: 5-bit elements, two words
+    rc, h = _create(lib, 20, w.coxeter(20), inv=1)
+    assert rc == 0 and lib.cg_growth_key_words(h) == 2 and lib.cg_growth_key_width(h) == 5
     lib.cg_growth_destroy(h)
 
 

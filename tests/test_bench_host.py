@@ -83,3 +83,20 @@ def test_reference_arm_runs_the_oracle():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--workload", "batch"], capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert out.returncode == 0 and "unavailable" in json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def test_generated_candidates_after_the_parent_edge_skip():
+    import bench
+    import workloads as w
+    lay = [1, 3, 6, 12]
+    # LRX: every generator's inverse is in the set, so each state after the first expands k - 1
+    assert bench.generated_candidates(5, w.lrx(5), lay, True, True) == 3 + 2 * (3 + 6 + 12)
+    assert bench.generated_candidates(5, w.lrx(5), lay, True, False) == 3 * sum(lay)
+    assert bench.generated_candidates(5, w.lrx(5), lay, False, True) == 3 + 2 * (3 + 6)
+    # LX is directed (L's inverse R is missing; X is an involution): it depends on the path
+    assert bench.generated_candidates(5, w.lx(5), lay, True, True) is None
+    # a directed set with no inverse present: nothing is skipped
+    c = w.cycle(5, [0, 1, 2, 3, 4])
+    assert bench.generated_candidates(5, [c], lay, True, True) == sum(lay)
+    # n = 16 keys carry no tag
+    assert bench.generated_candidates(16, w.coxeter(16), lay, True, True) == 15 * sum(lay)

@@ -37,19 +37,23 @@ def test_default_batch_matches_oracle(spec, reference):
 
 
 @pytest.mark.parametrize("opts", [
-    {"graph": True},
+    {"graph": False},
     {"visited": "hash"},
     {"visited": "bitmap", "ilp": 2},
     {"ilp": 3, "grid": 152},
     {"wave_l2": 1 << 16, "graph": True},
     {"wave_l2": -1, "grid": 300},
+    {"max_active": 7},
+    {"max_active": 1, "unit": 4},
+    {"unit": 2, "graph": False},
+    {"unit": 8, "visited": "hash"},
 ])
 def test_settings_do_not_change_results(cg, spec, reference, opts):
     with cg.Batch(spec, **opts) as b:
         for _ in range(3):              # first run plans (and captures), later runs replay
             assert [r.layers for r in b.run()] == reference
         st = b.stats()
-        assert st["launches"] >= 3
+        assert st["launches"] >= 2
 
 
 def test_graph_replay_after_option_change(cg, spec, reference):

@@ -60,6 +60,16 @@ def test_signatures_depend_on_workload_and_device():
 
 
 def test_batch_options_translation():
-    s = {"visited": "hash", "ilp": 2, "grid_per_sm": 3, "wave_l2": -1, "graph": True}
+    s = {"visited": "hash", "ilp": 2, "grid_per_sm": 3, "wave_l2": -1, "max_active": 512, "unit": 2,
+         "graph": True}
     assert tune.batch_options(s, 152) == {"visited": "hash", "ilp": 2, "grid": 456, "wave_l2": -1,
-                                          "graph": True}
+                                          "max_active": 512, "unit": 2, "graph": True}
+
+
+def test_batch_knobs_cover_visited_set_kind_chunking_and_graph():
+    names = [k for k, _ in tune.BATCH_KNOBS]
+    assert names == ["visited", "ilp", "grid_per_sm", "wave_l2", "max_active", "unit", "graph"]
+    values = dict(tune.BATCH_KNOBS)
+    assert set(values["visited"]) == {"auto", "hash", "bitmap"}
+    assert values["graph"][0] is True                   # the library default comes first
+    assert values["unit"][0] == 4 and values["max_active"][0] == 0
