@@ -86,7 +86,7 @@ def _ptr(a: np.ndarray, ctype):
 def growth(n: int, gens: Sequence[Sequence[int]], two_layer: bool = False,
            max_radius: int = -1, stop_above: int = 0, start=None) -> Tuple[List[int], int]:
     """Growth vector gamma(0..R) and the return code (0 ended, 1 stopped by a limit), from the
-    identity or from the vector `start` (n values in 0..15, repeats allowed)."""
+    identity (n <= 32) or from the vector `start` (n <= 64 values in 0..15, repeats allowed)."""
     lib = _load()
     g = _gens_array(n, gens)
     cap = 4096

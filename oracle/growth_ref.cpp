@@ -10,8 +10,9 @@
  * reach v), computed by the textbook breadth-first search the paper says all of its growth
  * algorithms are built on (Sections 3.1.2 and 3.1.3).  States are permutations held as byte
  * arrays; a generator g acts by gather, t[i] = s[g[i]].  The visited set is a
- * std::unordered_set of an injective 4-bit packing of the permutation, used only as a hash
- * key (n <= 16).
+ * std::unordered_set of an injective packing of the permutation, used only as a hash key:
+ * 4 bits per element for n <= 16, its bytes for n <= 32, 4 bits per value in 256 bits for
+ * vectors of up to 64 values below 16.
  *
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU baseline / reference arm may load
  * this file's library.  It shares no code, header or table with the CUDA library.
@@ -53,6 +54,18 @@ struct WideHash {
     size_t operator()(const WideKey& k) const {
         return std::hash<uint64_t>()(k.w[0] ^ (k.w[1] * 0x9E3779B97F4A7C15ull) ^
                                      (k.w[2] * 0xC2B2AE3D27D4EB4Full) ^ (k.w[3] * 0x165667B19E3779F9ull));
+    }
+};
+
+// Injective key of a permutation of up to 32 elements: its bytes, element i in byte i of a
+// 256-bit number (growth from the identity with 16 < n <= 32).
+struct ByteKeys {
+    using Key = WideKey;
+    using Set = std::unordered_set<WideKey, WideHash>;
+    static Key of(const uint8_t* p, int n) {
+        WideKey k{{0, 0, 0, 0}};
+        std::memcpy(k.w, p, (size_t)n);
+        return k;
     }
 };
 
@@ -169,7 +182,7 @@ int run_growth(B& bfs, int max_radius, uint64_t stop_above, uint64_t* out, int c
 extern "C" {
 
 /*
- * Growth vector of <gens> from the identity (oracle_growth, n <= 16) or from the vector `start`
+ * Growth vector of <gens> from the identity (oracle_growth, n <= 32) or from the vector `start`
  * (oracle_growth_from; n <= 64 values in 0..15, repeats allowed).
  *   two_layer   0: full visited set (any generating set); 1: keep only layers r-1 and r
  *               (correct only for inverse-closed sets; the tests check it against mode 0).
@@ -181,13 +194,17 @@ extern "C" {
  */
 int oracle_growth_from(int n, int k, const uint8_t* gens, const uint8_t* start, int two_layer,
                        int max_radius, uint64_t stop_above, uint64_t* out, int cap, int* num_layers) {
-    // n up to 64 when a start vector is given (values below 16), up to 16 from the identity
-    if (!valid_gens(n, k, gens, start ? 64 : 16) || num_layers == nullptr) return -1;
+    // n up to 64 when a start vector is given (values below 16), up to 32 from the identity
+    if (!valid_gens(n, k, gens, start ? 64 : 32) || num_layers == nullptr) return -1;
     if (start)
         for (int i = 0; i < n; ++i)
             if (start[i] > 15) return -1;
     if (n <= 16) {
         BfsT<NarrowKeys> bfs(n, k, gens, two_layer != 0, start);
+        return run_growth(bfs, max_radius, stop_above, out, cap, num_layers);
+    }
+    if (!start) {
+        BfsT<ByteKeys> bfs(n, k, gens, two_layer != 0, start);
         return run_growth(bfs, max_radius, stop_above, out, cap, num_layers);
     }
     BfsT<WideKeys> bfs(n, k, gens, two_layer != 0, start);

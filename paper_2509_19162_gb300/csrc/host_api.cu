@@ -87,11 +87,11 @@ void dev_free(void* p, cudaStream_t st) {
 }
 
 // ---- generators -------------------------------------------------------------------------
-bool is_perm_row(const uint8_t* g, int n) {   // n <= 64
-    uint64_t seen = 0;
+bool is_perm_row(const uint8_t* g, int n) {   // n <= 128
+    uint64_t seen[2] = {0, 0};
     for (int i = 0; i < n; ++i) {
-        if (g[i] >= n || (seen >> g[i]) & 1ull) return false;
-        seen |= 1ull << g[i];
+        if (g[i] >= n || (seen[g[i] >> 6] >> (g[i] & 63)) & 1ull) return false;
+        seen[g[i] >> 6] |= 1ull << (g[i] & 63);
     }
     return true;
 }
@@ -482,7 +482,7 @@ int ensure_small_buffers(cg_growth* h, cudaStream_t st) {
     h->d_ubeg = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 2, st);
     h->d_layers = (uint64_t*)dev_alloc(sizeof(uint64_t) * cg::kMaxLayers, st);
     if (!h->d_gens || !h->d_job || !h->d_ctl || !h->d_ubeg || !h->d_layers) return CG_ENOMEM;
-    if (h->k > 0) {
+    if (h->k > 0 && (int)h->gsm.size() == h->k) {   // one-word forms (two-word keys: none)
         cudaError_t e = cudaMemcpyAsync(h->d_gens, h->gsm.data(), sizeof(GenSM) * h->k,
                                         cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_rc(e);
@@ -1241,7 +1241,7 @@ int cg_growth_set_start(cg_growth_t h, const uint8_t* start) {
     h->width = w;
     h->wide = !use_narrow;
     if (use_narrow) h->gsm = make_gensms(h->rows, h->n, w);
-    else h->wgsm = wg;
+    else { h->wgsm = wg; h->gsm.clear(); }
     h->wstart = wkey;
     h->states_bound = std::min(h->order, rearr);
     return CG_OK;

@@ -147,7 +147,10 @@ def test_binary_reversals_large_n(cg, n):
 
 
 def test_long_vector_limits(cg):
-    with pytest.raises(RuntimeError):          # the identity of S_17 needs 5-bit elements
-        cg.growth(17, w.coxeter(17))
-    with pytest.raises(Exception):             # 62 elements of 2 bits do not fit 64 bits
-        cg.growth(62, w.coxeter(62), start=[3] + [0] * 61)
+    with pytest.raises(RuntimeError):          # the identity of S_26 needs more than 128 bits
+        cg.growth(26, w.coxeter(26), max_radius=2)
+    with pytest.raises(Exception):             # 33 elements of 4 bits do not fit 128 bits
+        cg.growth(33, w.coxeter(33), start=[5] + [0] * 32)
+    # 62 elements of 2 bits take two-word keys: the orbit of 3 0^61 is the 62 positions of the 3
+    r = cg.growth(62, w.coxeter(62), start=[3] + [0] * 61)
+    assert r.layers == [1] * 62

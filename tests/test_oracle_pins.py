@@ -371,3 +371,27 @@ def test_whole_s12_growth_oracle_b_equals_oracle_c(family):
     c = oracle.growth_bitmask(12, gens)
     assert b == c and b[1] == 0
     assert b[0] == _stored(f"s12_{family}_growth_b")
+
+
+# ---- growth from the identity beyond 16 elements (keys of the permutation's bytes) ----------
+
+@pytest.mark.parametrize("n", [17, 20, 24, 32])
+@pytest.mark.parametrize("two_layer", [False, True])
+def test_identity_beyond_16_is_mahonian_prefix(n, two_layer):
+    g, rc = oracle.growth(n, w.coxeter(n), two_layer=two_layer, max_radius=4)
+    assert rc == 1 and g == mahonian(n)[:5]
+
+
+@pytest.mark.parametrize("n", [17, 19])
+def test_identity_beyond_16_is_stirling_prefix(n):
+    c = stirling1_unsigned(n)
+    g, rc = oracle.growth(n, w.all_transpositions(n), max_radius=2)
+    assert g == [c[n - r] for r in range(3)]
+
+
+def test_identity_beyond_16_embeds_a_smaller_group():
+    # generators that move only the first 8 of 20 elements generate a copy of S_8: the growth
+    # of the whole orbit is that of S_8 Coxeter (40,320 states, diameter 28)
+    gens = [list(g) + list(range(8, 20)) for g in w.coxeter(8)]
+    g, rc = oracle.growth(20, gens)
+    assert rc == 0 and g == mahonian(8)
