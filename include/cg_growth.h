@@ -405,15 +405,14 @@ int cg_expand(int n, int k, const uint8_t* gens, const uint64_t* frontier, uint6
 int cg_hash_insert(uint64_t* table, uint64_t slots, const uint64_t* keys, uint64_t N,
                    uint64_t* new_out, uint64_t* new_count, void* cuda_stream);
 
-/* Fill a table of `slots` entries (device) with the empty marker.  Errors: CG_ECUDA. */
-
 /*
  * Radix sort + unique (the sort strategy's dedup step).  keys: device, n uint64 values whose bits
  * at and above key_bits are zero (packed keys of n-element permutations have key_bits = 4n);
- * sorted ascending in place (LSD radix sort, 8-bit digits, stable passes).  The distinct values,
+ * sorted ascending in place (LSD radix sort, 8-bit digits, one stable single-sweep pass per
+ * digit with a decoupled look-back per digit value).  The distinct values,
  * ascending, are written to out (device, room for n) and their number to *d_count (device
  * uint64).  scratch: device buffer of at least cg_sort_unique_scratch_bytes(n) bytes, owned by
- * the caller, contents undefined afterwards.  n < 2^32.  Asynchronous on the stream.
+ * the caller, contents undefined afterwards.  Asynchronous on the stream.
  * Errors: CG_EINVAL, CG_ECUDA.
  */
 size_t cg_sort_unique_scratch_bytes(uint64_t n);
@@ -421,15 +420,18 @@ int cg_sort_unique(uint64_t* keys, uint64_t n, int key_bits, uint64_t* out, uint
                    void* scratch, size_t scratch_bytes, void* cuda_stream);
 
 /*
- * Merge-path set difference (the sort strategy's removal of seen states): out = the distinct
+ * Set difference (the sort strategy's removal of seen states, K4): out = the distinct
  * values of a that occur in neither b nor c, ascending; *d_count = their number (device uint64).
  * a, b, c: device, each sorted ascending (a may hold duplicates; b or c may be NULL with length
- * 0).  scratch as for cg_sort_unique with n = na.  na < 2^32.  Asynchronous on the stream.
+ * 0).  scratch as for cg_sort_unique with n = na.  Asynchronous on the stream.
  * Errors: CG_EINVAL, CG_ECUDA.
  */
 int cg_set_difference(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
                       const uint64_t* c, uint64_t nc, uint64_t* out, uint64_t* d_count,
                       void* scratch, size_t scratch_bytes, void* cuda_stream);
+
+/* Fill a table of `slots` entries (device) with the empty marker of cg_hash_insert.
+ * Errors: CG_EINVAL (NULL table with slots > 0), CG_ECUDA. */
 int cg_hash_clear(uint64_t* table, uint64_t slots, void* cuda_stream);
 
 /*

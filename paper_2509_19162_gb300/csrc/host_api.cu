@@ -404,7 +404,8 @@ struct cg_growth {
 
     // sort strategy: three rotating sorted layers, candidate buffer, primitive scratch
     uint64_t* d_L[3] = {nullptr, nullptr, nullptr};
-    uint64_t L_cap = 0;
+    uint64_t L_caps[3] = {0, 0, 0};
+    uint64_t L_cap = 0;                          // largest of L_caps (reported in the stats)
     uint64_t* d_cand = nullptr;
     uint64_t cand_cap = 0;
     void* d_sort_scratch = nullptr;
@@ -464,6 +465,7 @@ struct cg_growth {
 
     void release_sort(cudaStream_t st) {
         for (auto& p : d_L) { dev_free(p, st); p = nullptr; }
+        for (auto& c : L_caps) c = 0;
         dev_free(d_cand, st);
         dev_free(d_sort_scratch, st);
         dev_free(d_count, st);
@@ -908,97 +910,160 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
 // sort, unique + merge-path difference against layers r and r-1, compaction (sort_path.cu).
 // The host reads |L_{r+1}| after each step to size the next one.
 
-int ensure_sort_buffers(cg_growth* h, uint64_t need_layer, uint64_t need_cand, uint64_t mem,
-                        cudaStream_t st, int cur, int prev, uint64_t Fcur, uint64_t Fprev) {
-    // grow candidate buffer + scratch
-    if (need_cand > h->cand_cap) {
-        uint64_t cap = std::max<uint64_t>(need_cand, std::min<uint64_t>(need_cand * 2, 1ull << 31));
-        cap = std::min<uint64_t>(cap, 0xFFFFFFFFull);
-        const size_t sb = cg::sort_scratch_bytes(cap);
-        const uint64_t layer_bytes = 3 * std::max(h->L_cap, need_layer) * 8;
-        if (cap * 8 + sb + layer_bytes > mem) {
-            cap = need_cand;
-            if (cap * 8 + cg::sort_scratch_bytes(cap) + layer_bytes > mem) return CG_TRUNC_MEMCAP;
-        }
-        dev_free(h->d_cand, st);
-        dev_free(h->d_sort_scratch, st);
-        h->d_cand = (uint64_t*)dev_alloc(cap * 8, st);
-        h->d_sort_scratch = dev_alloc(cg::sort_scratch_bytes(cap), st);
-        h->cand_cap = cap;
-        if (!h->d_cand || !h->d_sort_scratch) return CG_ENOMEM;
+// Bytes of the candidate buffer and sort scratch for q candidates.
+uint64_t cand_bytes(uint64_t q) { return q * 8 + cg::sort_scratch_bytes(q); }
+
+// Candidate buffer and scratch for q candidates (kept when larger, unless shrink).
+int ensure_cand(cg_growth* h, uint64_t q, cudaStream_t st, bool shrink = false) {
+    if (h->d_cand && (q == h->cand_cap || (q < h->cand_cap && !shrink))) return CG_OK;
+    dev_free(h->d_cand, st);
+    dev_free(h->d_sort_scratch, st);
+    h->d_cand = (uint64_t*)dev_alloc(q * 8, st);
+    h->d_sort_scratch = dev_alloc(cg::sort_scratch_bytes(q), st);
+    h->cand_cap = q;
+    if (!h->d_cand || !h->d_sort_scratch) return CG_ENOMEM;
+    return CG_OK;
+}
+
+// Layer buffer i with room for cap keys, keeping its first `keep` keys.
+int ensure_layer(cg_growth* h, int i, uint64_t cap, uint64_t keep, cudaStream_t st) {
+    if (cap <= h->L_caps[i] && h->d_L[i]) return CG_OK;
+    uint64_t* nb = (uint64_t*)dev_alloc(std::max<uint64_t>(cap, 1) * 8, st);
+    if (!nb) return CG_ENOMEM;
+    if (keep && h->d_L[i]) {
+        cudaError_t e = cudaMemcpyAsync(nb, h->d_L[i], keep * 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { dev_free(nb, st); return cuda_rc(e); }
     }
-    if (need_layer > h->L_cap) {
-        uint64_t cap = std::max<uint64_t>(need_layer, std::min<uint64_t>(need_layer * 2, h->states_bound));
-        if (3 * cap * 8 + h->cand_cap * 8 + cg::sort_scratch_bytes(h->cand_cap) > mem) cap = need_layer;
-        if (3 * cap * 8 + h->cand_cap * 8 + cg::sort_scratch_bytes(h->cand_cap) > mem) return CG_TRUNC_MEMCAP;
-        for (int i = 0; i < 3; ++i) {
-            uint64_t* nb = (uint64_t*)dev_alloc(cap * 8, st);
-            if (!nb) return CG_ENOMEM;
-            const uint64_t keep = (i == cur) ? Fcur : (i == prev ? Fprev : 0);
-            if (keep && h->d_L[i]) {
-                cudaError_t e = cudaMemcpyAsync(nb, h->d_L[i], keep * 8, cudaMemcpyDeviceToDevice, st);
-                if (e != cudaSuccess) return cuda_rc(e);
-            }
-            dev_free(h->d_L[i], st);
-            h->d_L[i] = nb;
-        }
-        h->L_cap = cap;
-    }
+    dev_free(h->d_L[i], st);
+    h->d_L[i] = nb;
+    h->L_caps[i] = std::max<uint64_t>(cap, 1);
+    h->L_cap = std::max(h->L_cap, h->L_caps[i]);
     return CG_OK;
 }
 
 // Layer steps of the sort strategy from layer `radius` (d_L[cur], Fcur keys) and layer radius-1
 // (d_L[prev], Fprev keys), both sorted; sort_layers holds |L_0| .. |L_radius|.
+//
+// A step whose k Fcur candidates fit the memory cap at once is: candidate histograms + radix
+// passes (expand fused, sorted candidates in d_cand), then first-of-run + difference against
+// L_r and L_{r-1} + compaction into the scratch, copied into the next layer's buffer.  Larger
+// steps run in key-range chunks: the top-digit histogram of all candidates splits the digit
+// values into ranges of at most the candidate capacity; per range the candidates are generated
+// again and kept when they fall in it, sorted, and differenced -- the ranges are disjoint and
+// ascending, so their survivors append to layer r+1 in order.
 int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, uint64_t Fprev,
                int radius, int* final_status) {
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
     const int bits = h->width * h->n;
+    const int P = cg::sort_passes(bits);
+    const int top_shift = 8 * (P - 1);
     int nxt = 3 - cur - prev;
-    int rc = CG_OK;
     cudaError_t e = cudaSuccess;
+    int rc = CG_OK;
     if (!h->ev0) {
         if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
         if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
     }
+    auto fail_mem = [](int r) { return r == CG_ENOMEM || r == CG_TRUNC_MEMCAP; };
     int status = cg::kRunning;
     while (status == cg::kRunning) {
         if (h->max_radius >= 0 && radius >= h->max_radius) { status = cg::kTruncRadius; break; }
         const uint64_t C = (uint64_t)h->k * Fcur;
-        if (C >= 0xFFFFFFFFull) { status = cg::kNeedMem; break; }
-        rc = ensure_sort_buffers(h, Fcur, C, mem, st, cur, prev, Fcur, Fprev);
-        if (rc == CG_TRUNC_MEMCAP) { status = cg::kNeedMem; break; }
+        // the next layer's first buffer: the growth ratio of the last step, with a margin
+        const double ratio = Fprev > 0 ? (double)Fcur / (double)Fprev : (double)h->k;
+        uint64_t est = (uint64_t)std::min<double>((double)C, std::max(1024.0, 1.2 * ratio * (double)Fcur));
+        est = std::min<uint64_t>(est, h->states_bound);
+        // the candidates' share of the memory cap, beside the three layers (held or planned)
+        const uint64_t held_layers = 8 * (std::max(h->L_caps[cur], Fcur) + std::max(h->L_caps[prev], Fprev) +
+                                          std::max(h->L_caps[nxt], est));
+        if (held_layers + cand_bytes(4096) >= mem) { status = cg::kNeedMem; break; }
+        uint64_t Q = std::min<uint64_t>(C, (mem - held_layers) * 2 / 33);   // 16.5 bytes a candidate
+        while (Q > 4096 && held_layers + cand_bytes(Q) > mem) Q -= Q / 64 + 1;
+        if (h->cand_cap >= C && held_layers + cand_bytes(h->cand_cap) <= mem) Q = C;   // allocated
+        if (Q < std::min<uint64_t>(C, 4096)) { status = cg::kNeedMem; break; }
+        // a larger buffer from an earlier step is kept while it fits beside the layers
+        rc = ensure_cand(h, Q, st, held_layers + cand_bytes(h->cand_cap) > mem);
+        if (rc == CG_OK) rc = ensure_layer(h, nxt, est, 0, st);
+        if (fail_mem(rc)) { status = cg::kNeedMem; break; }
         if (rc) return rc;
         cg::SortScratch sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
-        if ((e = cudaMemsetAsync(sc.err, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
-        if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
-        if ((e = cg::launch_expand_all(h->d_gens, h->k, h->d_L[cur], Fcur, h->d_cand, st)) != cudaSuccess)
-            return cuda_rc(e);
-        if ((e = cg::launch_radix_sort(h->d_cand, C, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+        const cg::ExpandSrc src{h->d_gens, h->k, h->d_L[cur], Fcur};
         const uint64_t* bs[2] = {h->d_L[cur], h->d_L[prev]};
         const unsigned long long nbs[2] = {Fcur, Fprev};
-        if ((e = cg::launch_unique_difference(h->d_cand, C, bs, nbs, 2, sc.keys_tmp, h->d_count, sc, st)) !=
-            cudaSuccess)
-            return cuda_rc(e);
-        if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
-        const int passes = (bits + 7) / 8;
-        h->stats.launches += 1 + 3 * passes + 2 + 1;
-        unsigned long long Fn = 0;
-        int derr = 0;
-        if ((e = cudaMemcpyAsync(&Fn, h->d_count, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
-        if ((e = cudaMemcpyAsync(&derr, sc.err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
-        h->stats.d2h_bytes += 12;
-        h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
+        if ((e = cudaMemsetAsync(sc.err, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
+        // key ranges of top-digit values [lo, hi): one range when everything fits
+        std::vector<std::pair<unsigned, unsigned>> ranges;
+        if (C <= h->cand_cap) {
+            ranges.push_back({0u, 256u});
+        } else {
+            if ((e = cg::launch_candidate_hist(src, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+            std::vector<unsigned long long> th(256);
+            if ((e = cudaMemcpyAsync(th.data(), sc.ghist + (size_t)(P - 1) * 256, 256 * 8, cudaMemcpyDeviceToHost,
+                                     st)) != cudaSuccess)
+                return cuda_rc(e);
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+            h->stats.launches += 1;
+            h->stats.d2h_bytes += 256 * 8;
+            unsigned lo = 0;
+            uint64_t acc = 0;
+            bool ok = true;
+            for (unsigned d = 0; d < 256 && ok; ++d) {
+                if (th[d] > h->cand_cap) ok = false;            // one digit value alone is too many
+                else if (acc + th[d] > h->cand_cap) { ranges.push_back({lo, d}); lo = d; acc = th[d]; }
+                else acc += th[d];
+            }
+            if (!ok) { status = cg::kNeedMem; break; }
+            ranges.push_back({lo, 256u});
+        }
+        uint64_t Fn = 0;
+        bool stop_mem = false;
+        for (const auto& rg : ranges) {
+            if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
+            uint64_t Cc = C;
+            if (ranges.size() == 1) {
+                if ((e = cg::launch_expand_sort(src, h->d_cand, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+                h->stats.launches += 1 + P;
+            } else {
+                if ((e = cg::launch_expand_filter(src, top_shift, rg.first, rg.second, h->d_cand, h->cand_cap,
+                                                  h->d_count, sc.err, st)) != cudaSuccess)
+                    return cuda_rc(e);
+                unsigned long long got = 0;
+                if ((e = cudaMemcpyAsync(&got, h->d_count, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                    return cuda_rc(e);
+                if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+                Cc = std::min<uint64_t>(got, h->cand_cap);
+                if ((e = cg::launch_radix_sort(h->d_cand, Cc, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+                h->stats.launches += 2 + P;
+            }
+            if ((e = cg::launch_unique_difference(h->d_cand, Cc, bs, nbs, 2, sc.keys_tmp, h->d_count, sc, st)) !=
+                cudaSuccess)
+                return cuda_rc(e);
+            if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
+            h->stats.launches += 1;
+            unsigned long long Fc = 0;
+            int derr = 0;
+            if ((e = cudaMemcpyAsync(&Fc, h->d_count, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaMemcpyAsync(&derr, sc.err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+            h->stats.d2h_bytes += 12;
+            h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
+            if (derr) return derr;
+            if (Fc == 0) continue;
+            // append to the next layer, growing its buffer when the estimate was short
+            if (Fn + Fc > h->L_caps[nxt]) {
+                const uint64_t want = std::max<uint64_t>(Fn + Fc, h->L_caps[nxt] + h->L_caps[nxt] / 2);
+                rc = ensure_layer(h, nxt, std::min<uint64_t>(want, std::max<uint64_t>(C, Fn + Fc)), Fn, st);
+                if (fail_mem(rc)) { stop_mem = true; break; }
+                if (rc) return rc;
+            }
+            if ((e = cudaMemcpyAsync(h->d_L[nxt] + Fn, sc.keys_tmp, Fc * 8, cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess)
+                return cuda_rc(e);
+            Fn += Fc;
+        }
         h->stats.rounds += 1;
-        if (derr) return derr;
+        if (stop_mem) { status = cg::kNeedMem; break; }
         if (Fn == 0) { status = cg::kDone; break; }
-        // place L_{r+1} in the free layer buffer
-        rc = ensure_sort_buffers(h, Fn, C, mem, st, cur, prev, Fcur, Fprev);
-        if (rc == CG_TRUNC_MEMCAP) { status = cg::kNeedMem; break; }
-        if (rc) return rc;
-        sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
-        if ((e = cudaMemcpyAsync(h->d_L[nxt], sc.keys_tmp, Fn * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return cuda_rc(e);
         h->sort_layers.push_back(Fn);
         ++radius;
         const int old_prev = prev;
@@ -1010,6 +1075,7 @@ int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, 
         if (h->stop_above > 0 && Fn > h->stop_above) { status = cg::kTruncAbove; break; }
         if ((int)h->sort_layers.size() >= cg::kMaxLayers) { status = cg::kTruncRadius; break; }
     }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
     h->host_job.radius = radius;
     h->host_job.status = status;
     h->last_layer_ptr = h->d_L[cur];
@@ -1029,10 +1095,10 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
         h->d_count = (unsigned long long*)dev_alloc(64, st);
         if (!h->d_count) return CG_ENOMEM;
     }
-    const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
     h->sort_layers.assign(1, 1);
-    rc = ensure_sort_buffers(h, 1, std::max<uint64_t>(h->k, 1), mem, st, 0, 1, 0, 0);
-    if (rc) return rc < 0 ? rc : CG_ENOMEM;
+    if ((rc = ensure_cand(h, std::max<uint64_t>((uint64_t)h->k, 4096), st))) return rc;
+    if ((rc = ensure_layer(h, 0, 1, 0, st))) return rc;
+    if ((rc = ensure_layer(h, 1, 1, 0, st))) return rc;
     uint64_t id = 0;
     for (int i = 0; i < h->n; ++i) id |= (uint64_t)i << (4 * i);
     if (h->use_start) id = h->start_key;
@@ -1045,10 +1111,12 @@ int run_sort(cg_growth* h, cudaStream_t st, int* final_status) {
 
 // AUTO, undirected generating set: when the states stored by the visited-set path outgrow
 // mem_cap, the growth goes on with the sorted layer step, which keeps only the last two layers
-// (in an undirected graph the neighbours of layer r lie in layers r-1, r and r+1).  Layers
-// L_{r-1} and L_r are read back, stripped of their parent-edge tags and sorted; the key store
-// and the visited set are released first.  Nothing changes (the truncation stands) when the
-// sorted step's buffers for layer r would not fit mem_cap either.
+// (in an undirected graph the neighbours of layer r lie in layers r-1, r and r+1).  The visited
+// set is released, layers L_{r-1} and L_r are copied on the device into the sorted step's layer
+// buffers (while the key store still exists the job holds up to their size beyond what it held),
+// stripped of their parent-edge tags and sorted, and the key store is released.  Nothing
+// changes (the truncation stands) when the two layers and a minimal candidate buffer would not
+// fit mem_cap.
 int continue_sorted(cg_growth* h, cudaStream_t st, int* final_status) {
     const JobDev J = h->host_job;
     const int r = J.radius;
@@ -1062,49 +1130,43 @@ int continue_sorted(cg_growth* h, cudaStream_t st, int* final_status) {
     h->stats.d2h_bytes += sizeof(uint64_t) * sizes.size();
     const uint64_t Fprev = r > 0 ? sizes[r - 1] : 0;
     if (sizes[r] != Fcur || J.lo < Fprev) return CG_EDEVICE;
-    // the sorted step's first buffers, as ensure_sort_buffers sizes them at their smallest
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
-    const uint64_t need_layer = std::max<uint64_t>(std::max(Fcur, Fprev), 1);
-    const uint64_t need_cand = std::max<uint64_t>(std::max<uint64_t>((uint64_t)h->k * Fcur, Fprev), 1);
-    if (need_cand >= 0xFFFFFFFFull ||
-        3 * need_layer * 8 + need_cand * 8 + cg::sort_scratch_bytes(need_cand) > mem)
-        return CG_OK;
-    std::vector<uint64_t> keys(Fprev + Fcur);
-    if (!keys.empty()) {
-        e = cudaMemcpyAsync(keys.data(), h->d_keys + (J.lo - Fprev), keys.size() * 8,
-                            cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_rc(e);
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
-        h->stats.d2h_bytes += keys.size() * 8;
-    }
-    if (h->n * h->width <= 60)
-        for (auto& x : keys) x &= cg::kKeyBits60;
-    dev_free(h->d_keys, st);
-    dev_free(h->d_table, st);
-    h->d_keys = nullptr;
-    h->d_table = nullptr;
-    h->keys_cap = h->table_slots = 0;
-    h->last_layer_ptr = nullptr;
-    h->last_layer_n = 0;
+    // the first candidate buffer sorts the two layers; the steps size their own
+    const uint64_t q0 = std::max<uint64_t>(std::max<uint64_t>(Fprev, Fcur), 4096);
+    if (8 * (Fprev + Fcur) + cand_bytes(q0) > mem) return CG_OK;
     if (!h->d_count) {
         h->d_count = (unsigned long long*)dev_alloc(64, st);
         if (!h->d_count) return CG_ENOMEM;
     }
+    dev_free(h->d_table, st);
+    h->d_table = nullptr;
+    h->table_slots = 0;
     const int cur = 0, prev = 1;
-    int rc = ensure_sort_buffers(h, need_layer, need_cand, mem, st, cur, prev, 0, 0);
-    if (rc) return rc < 0 ? rc : CG_ENOMEM;
-    if (Fprev) {
-        if ((e = cudaMemcpyAsync(h->d_L[prev], keys.data(), Fprev * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_rc(e);
-    }
-    if ((e = cudaMemcpyAsync(h->d_L[cur], keys.data() + Fprev, Fcur * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    int rc = ensure_layer(h, prev, std::max<uint64_t>(Fprev, 1), 0, st);
+    if (rc == CG_OK) rc = ensure_layer(h, cur, std::max<uint64_t>(Fcur, 1), 0, st);
+    if (rc) return rc;
+    if (Fprev && (e = cudaMemcpyAsync(h->d_L[prev], h->d_keys + (J.lo - Fprev), Fprev * 8,
+                                      cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return cuda_rc(e);
-    h->stats.h2d_bytes += keys.size() * 8;
+    if ((e = cudaMemcpyAsync(h->d_L[cur], h->d_keys + J.lo, Fcur * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_rc(e);
+    dev_free(h->d_keys, st);
+    h->d_keys = nullptr;
+    h->keys_cap = 0;
+    h->last_layer_ptr = nullptr;
+    h->last_layer_n = 0;
+    if ((rc = ensure_cand(h, q0, st))) return rc;
+    if (h->n * h->width <= 60) {
+        if ((e = cg::launch_mask_keys(h->d_L[prev], Fprev, cg::kKeyBits60, st)) != cudaSuccess) return cuda_rc(e);
+        if ((e = cg::launch_mask_keys(h->d_L[cur], Fcur, cg::kKeyBits60, st)) != cudaSuccess) return cuda_rc(e);
+        h->stats.launches += 2;
+    }
     const cg::SortScratch sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
     const int bits = h->width * h->n;
+    if ((e = cudaMemsetAsync(sc.err, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
     if ((e = cg::launch_radix_sort(h->d_L[prev], Fprev, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
     if ((e = cg::launch_radix_sort(h->d_L[cur], Fcur, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
-    h->stats.launches += 2 * 3 * ((bits + 7) / 8);
+    h->stats.launches += 2 * (1 + cg::sort_passes(bits));
     h->sort_layers.assign(sizes.begin(), sizes.end());
     h->stats.switched_to_sort = 1;
     h->stats.sort_from = r;
@@ -1472,7 +1534,7 @@ size_t cg_sort_unique_scratch_bytes(uint64_t n) { return cg::sort_scratch_bytes(
 
 int cg_sort_unique(uint64_t* keys, uint64_t n, int key_bits, uint64_t* out, uint64_t* d_count,
                    void* scratch, size_t scratch_bytes, void* cuda_stream) {
-    if (key_bits < 1 || key_bits > 64 || !d_count || n >= 0xFFFFFFFFull) return CG_EINVAL;
+    if (key_bits < 1 || key_bits > 64 || !d_count) return CG_EINVAL;
     if (n > 0 && (!keys || !out || !scratch)) return CG_EINVAL;
     if (n > 0 && scratch_bytes < cg::sort_scratch_bytes(n)) return CG_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1489,7 +1551,7 @@ int cg_sort_unique(uint64_t* keys, uint64_t n, int key_bits, uint64_t* out, uint
 int cg_set_difference(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
                       const uint64_t* c, uint64_t nc, uint64_t* out, uint64_t* d_count,
                       void* scratch, size_t scratch_bytes, void* cuda_stream) {
-    if (!d_count || na >= 0xFFFFFFFFull) return CG_EINVAL;
+    if (!d_count) return CG_EINVAL;
     if ((na > 0 && (!a || !out || !scratch)) || (nb > 0 && !b) || (nc > 0 && !c)) return CG_EINVAL;
     if (na > 0 && scratch_bytes < cg::sort_scratch_bytes(na)) return CG_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -9,27 +9,58 @@
 
 namespace cg {
 
-// Device scratch of the sort primitives for up to n keys, carved from one caller buffer.
+// Device scratch of the sort primitives for up to n keys, carved from one caller buffer:
+// a ping-pong key buffer, the digit histograms of every pass, and the control words and
+// look-back descriptors that the single-pass (per digit) scatter and the compaction chain
+// their tiles with.
 struct SortScratch {
-    uint64_t* keys_tmp;                 // n keys (ping-pong buffer, also compaction output)
-    unsigned* hist;                     // per-tile digit histograms / scanned offsets
-    unsigned long long* scan_desc;      // look-back descriptors of the histogram scan
-    unsigned long long* compact_desc;   // look-back descriptors of the compaction
-    unsigned char* flags;               // n keep-flags
-    unsigned* tickets;                  // [0] scan, [1] compaction
-    int* err;                           // 0 or a CG_E* code
+    uint64_t* keys_tmp;                 // n keys
+    int* err;                           // 0 or a CG_E* code (cleared by the caller)
+    unsigned long long* ghist;          // kSortMaxPasses x 256 digit counts
+    unsigned* ctl;                      // tile tickets: [p] pass p, [15] the compaction
+    unsigned long long* desc;           // look-back descriptors: tiles x 256
     unsigned long long n;
+    size_t reset_bytes;                 // bytes from ghist that a sort clears (to the end)
 };
+
+constexpr int kSortMaxPasses = 8;
 
 size_t sort_scratch_bytes(unsigned long long n);
 SortScratch carve_sort_scratch(void* scratch, unsigned long long n);
 
+// Candidates generated on the fly: candidate i of [0, k F) is generator i / F applied to
+// frontier[i % F] (expand fused into the sort's first reads).
+struct ExpandSrc {
+    const GenSM* gens;
+    int k;
+    const uint64_t* frontier;
+    unsigned long long F;
+};
+
 cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,
                               uint64_t* out, cudaStream_t st);
+// Sort keys[0, n) ascending on their low `bits` bits (higher bits zero), in place.
 cudaError_t launch_radix_sort(uint64_t* keys, unsigned long long n, int bits, const SortScratch& s,
                               cudaStream_t st);
+// Generate the k F candidates of src and write them sorted to out (k F keys, not s.keys_tmp).
+cudaError_t launch_expand_sort(const ExpandSrc& src, uint64_t* out, int bits, const SortScratch& s,
+                               cudaStream_t st);
+// out = the keys of sorted a that are first of their run and absent from every sorted b_j (at
+// most 2 sets), in order; *d_count = their number.
 cudaError_t launch_unique_difference(const uint64_t* a, unsigned long long na, const uint64_t* const* bs,
                                      const unsigned long long* nbs, int nb_sets, uint64_t* out,
                                      unsigned long long* d_count, const SortScratch& s, cudaStream_t st);
+
+// 8-bit LSD passes over `bits` key bits.
+int sort_passes(int bits);
+// Digit histograms (s.ghist[p * 256 + d], every pass p) of the candidates of src.
+cudaError_t launch_candidate_hist(const ExpandSrc& src, int bits, const SortScratch& s, cudaStream_t st);
+// The candidates of src whose digit at `shift` lies in [d0, d1), appended to out (cap keys) in no
+// particular order; *d_count receives their number (d_err set if out is too small).
+cudaError_t launch_expand_filter(const ExpandSrc& src, int shift, unsigned d0, unsigned d1, uint64_t* out,
+                                 unsigned long long cap, unsigned long long* d_count, int* d_err,
+                                 cudaStream_t st);
+// keys[i] &= mask, i < n.
+cudaError_t launch_mask_keys(uint64_t* keys, unsigned long long n, uint64_t mask, cudaStream_t st);
 
 }  // namespace cg

@@ -1,19 +1,22 @@
 // Sort strategy of the growth library: sorted layers, radix sort + unique of the candidates,
-// merge-path set difference against the two previous layers, compaction.
+// set difference against the two previous layers, compaction.
 //
 // For an inverse-closed generating set every neighbour of layer r lies in layer r-1, r or r+1,
 // so layer r+1 = unique(candidates) \ (L_r U L_{r-1}) needs only the two previous layers
 // (Section 3.4: undirected graphs are those with inverse-closed generators).  Layers are kept
-// as arrays of packed keys sorted ascending.  Per layer step:
-//   expand        candidates = every generator applied to every state of L_r
-//   radix sort    LSD, 8-bit digits over the w n significant key bits (w = 4 bits per element
-//                 for permutations, 1 or 2 for narrow coset vectors); per pass: per-tile digit
-//                 histograms, one device-wide scan (decoupled look-back), stable scatter with
-//                 warp match_any ranking
-//   unique + diff one merge-path kernel per previous layer flags the candidates that are the
-//                 first of their run and absent from that layer
-//   compaction    single-pass decoupled look-back over tiles; the flagged keys, in order, are
-//                 layer r+1 (still sorted) and their number is |L_{r+1}|
+// as arrays of packed keys sorted ascending.  One layer step is:
+//   histograms    one read of the candidates -- generated on the fly from L_r (every generator
+//                 on every state: the expand is fused, candidates are never written unsorted)
+//                 -- counts the 8-bit digits of every pass at once
+//   radix passes  LSD over the w n significant key bits, one kernel per pass: each 4096-key
+//                 tile ranks its keys by digit (warp match_any, per-warp digit counts in shared
+//                 memory), finds each digit's offset among the earlier tiles by a decoupled
+//                 look-back per digit, and writes its keys digit run by digit run (coalesced)
+//                 from a shared-memory staging copy; stable, so the passes compose
+//   difference    one kernel: a candidate survives when it is the first of its run and absent
+//                 from L_r and L_{r-1} (a galloping walk through each sorted layer from the
+//                 thread's first key), and the survivors are compacted in order with a
+//                 decoupled look-back over tiles: layer r+1, sorted, and its size
 // The same primitives back the step-level entry points cg_sort_unique and cg_set_difference.
 #include <cstdint>
 
@@ -27,89 +30,105 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kItems = 16;                       // keys per thread per tile
 constexpr int kTile = kBlock * kItems;           // 4096 keys per tile
+constexpr int kWarps = kBlock / 32;
 constexpr int kRadixBits = 8;
 constexpr int kDigits = 1 << kRadixBits;
 constexpr uint64_t kSpinTimeoutNs = 5ull * 1000 * 1000 * 1000;
 
 // ---- decoupled look-back ---------------------------------------------------------------------
-// Tile descriptor: bits 62-63 = status (0 none, 1 aggregate, 2 inclusive prefix), bits 0-61 =
-// value.  Tiles take tickets in start order, so every predecessor a tile waits on is running.
-constexpr unsigned long long kStatusShift = 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+// Descriptor: bits 60-63 epoch (which pass wrote it; the region is cleared once per sort),
+// bits 58-59 status (1 aggregate of the tile, 2 inclusive prefix), bits 0-57 value.  Tiles take
+// tickets in start order, so every predecessor a tile waits on is running.
+constexpr unsigned long long kValMask = (1ull << 58) - 1;
 
-__device__ __forceinline__ void publish(unsigned long long* desc, int tile, unsigned long long status,
-                                        unsigned long long value) {
-    __threadfence();
-    atomicExch(desc + tile, (status << kStatusShift) | (value & kValueMask));
+__device__ __forceinline__ unsigned long long make_desc(unsigned epoch, unsigned status, unsigned long long v) {
+    return ((unsigned long long)epoch << 60) | ((unsigned long long)status << 58) | (v & kValMask);
 }
 
-// Exclusive prefix of `aggregate` over tiles [0, tile); called by one thread.  Returns false
-// (and sets *err) if a predecessor never published within the time limit.
-__device__ bool look_back(unsigned long long* desc, int tile, unsigned long long aggregate,
-                          unsigned long long* prefix_out, int* err) {
+// Exclusive prefix of `agg` over the tiles before `tile`, for one lane of descriptors
+// (desc[t * stride]).  The walk back reads kWindow predecessors' descriptors per round trip
+// (independent loads), sums aggregates in order and stops at the first inclusive prefix; a
+// window with an unpublished descriptor is read again from there.  Sets *err and returns 0 if
+// a predecessor never publishes in time.
+constexpr int kWindow = 8;
+
+__device__ unsigned long long look_back(unsigned long long* desc, int stride, int tile, unsigned long long agg,
+                                        unsigned epoch, int* err) {
     if (tile == 0) {
-        publish(desc, 0, 2, aggregate);
-        *prefix_out = 0;
-        return true;
+        atomicExch(desc, make_desc(epoch, 2, agg));
+        return 0;
     }
-    publish(desc, tile, 1, aggregate);
+    atomicExch(desc + (size_t)tile * stride, make_desc(epoch, 1, agg));
     unsigned long long prefix = 0;
     int t = tile - 1;
     const uint64_t t0 = globaltimer_ns();
-    while (t >= 0) {
-        const unsigned long long d = ld_relaxed_ull(desc + t);
-        const unsigned long long st = d >> kStatusShift;
-        if (st == 0) {
+    unsigned spins = 0;
+    bool done = false;
+    while (!done) {
+        unsigned long long d[kWindow];
+#pragma unroll
+        for (int i = 0; i < kWindow; ++i)
+            d[i] = t - i >= 0 ? ld_relaxed_ull(desc + (size_t)(t - i) * stride) : 0;
+        int used = 0;
+        bool stalled = false;
+#pragma unroll
+        for (int i = 0; i < kWindow; ++i) {
+            if (done || stalled || t - i < 0) continue;
+            const unsigned st = (unsigned)(d[i] >> 58) & 3u;
+            if ((unsigned)(d[i] >> 60) != epoch || st == 0) { stalled = true; continue; }
+            prefix += d[i] & kValMask;
+            ++used;
+            if (st == 2) done = true;
+        }
+        t -= used;
+        if (t < 0) done = true;            // never reached: tile 0 publishes an inclusive prefix
+        if (!done && stalled && (++spins & 7u) == 0) {
+            if (*(volatile int*)err != 0) return 0;
             if (globaltimer_ns() - t0 > kSpinTimeoutNs) {
                 atomicCAS(err, 0, CG_ETIMEOUT);
-                return false;
+                return 0;
             }
-            if (*(volatile int*)err != 0) return false;
-            __nanosleep(64);
-            continue;
         }
-        prefix += d & kValueMask;
-        if (st == 2) break;
-        --t;
     }
-    __threadfence();
-    publish(desc, tile, 2, prefix + aggregate);
-    *prefix_out = prefix;
-    return true;
+    atomicExch(desc + (size_t)tile * stride, make_desc(epoch, 2, prefix + agg));
+    return prefix;
 }
 
-// Block-wide exclusive scan of one value per thread (kBlock threads).  Returns the exclusive
-// prefix; *total receives the block sum.
-__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* total) {
-    __shared__ unsigned s_w[kBlock / 32];
+// Block-wide exclusive scan of one value per thread (kBlock threads); *total = block sum.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* total) {
+    __shared__ T s_w[kWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_w[w] = x;
     __syncthreads();
     if (w == 0) {
-        unsigned s = lane < kBlock / 32 ? s_w[lane] : 0;
+        T s = lane < kWarps ? s_w[lane] : T(0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+            const T y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
-        if (lane < kBlock / 32) s_w[lane] = s;
+        if (lane < kWarps) s_w[lane] = s;
     }
     __syncthreads();
-    const unsigned excl = (w ? s_w[w - 1] : 0) + x - v;
-    *total = s_w[kBlock / 32 - 1];
+    const T excl = (w ? s_w[w - 1] : T(0)) + x - v;
+    *total = s_w[kWarps - 1];
     __syncthreads();
     return excl;
 }
 
-// ---- expand ------------------------------------------------------------------------------------
-// out[j*F + i] = gens[j](in[i]).  The generators are staged in shared memory when they fit in
-// kExpandSmem bytes, else read through L1.
+__device__ __forceinline__ uint64_t gen_candidate(const ExpandSrc& src, unsigned long long i) {
+    const unsigned g = (unsigned)(i / src.F);
+    return apply_gen(src.gens[g], src.frontier[i - (unsigned long long)g * src.F]);
+}
+
+// ---- expand (standalone: the step-level cg_expand and the memory hand-off) ----------------
 constexpr size_t kExpandSmem = 32 << 10;
 
 template <bool kSmem>
@@ -129,214 +148,239 @@ __global__ void expand_all_kernel(const GenSM* __restrict__ gens, int k, const u
     }
 }
 
-// ---- radix sort --------------------------------------------------------------------------------
-// Digit histogram of each tile, stored digit-major: hist[d * ntiles + tile].
+// ---- digit histograms of every pass in one read ------------------------------------------
+template <bool kGen>
 __global__ void __launch_bounds__(kBlock)
-radix_hist_kernel(const uint64_t* __restrict__ keys, unsigned long long n, int shift,
-                  unsigned* __restrict__ hist, int ntiles) {
-    __shared__ unsigned s_h[kDigits];
-    for (int d = threadIdx.x; d < kDigits; d += kBlock) s_h[d] = 0;
+hist_all_kernel(const uint64_t* __restrict__ keys, ExpandSrc src, unsigned long long n, int passes,
+                unsigned long long* __restrict__ ghist) {
+    __shared__ unsigned s_h[kSortMaxPasses][kDigits];
+    for (int i = threadIdx.x; i < kSortMaxPasses * kDigits; i += kBlock) (&s_h[0][0])[i] = 0;
     __syncthreads();
-    const unsigned long long base = (unsigned long long)blockIdx.x * kTile;
-#pragma unroll 4
-    for (int i = 0; i < kItems; ++i) {
-        const unsigned long long e = base + (unsigned long long)i * kBlock + threadIdx.x;
-        if (e < n) atomicAdd(&s_h[(keys[e] >> shift) & (kDigits - 1)], 1u);
+    const unsigned long long stride = (unsigned long long)gridDim.x * kBlock;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)kBlock + threadIdx.x; i < n; i += stride) {
+        const uint64_t key = kGen ? gen_candidate(src, i) : keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(key >> (kRadixBits * p)) & (kDigits - 1)], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kDigits; d += kBlock) hist[(size_t)d * ntiles + blockIdx.x] = s_h[d];
+    for (int i = threadIdx.x; i < passes * kDigits; i += kBlock) {
+        const unsigned c = (&s_h[0][0])[i];
+        if (c) atomicAdd(ghist + i, (unsigned long long)c);
+    }
 }
 
-// Exclusive scan in place of a u32 array of length n (< 2^32 total), tiles of kTile entries,
-// decoupled look-back.  desc must be zeroed (one entry per tile); ticket zeroed.
-__global__ void __launch_bounds__(kBlock)
-scan_u32_kernel(unsigned* data, unsigned long long n, unsigned long long* desc, unsigned* ticket,
-                int* err) {
+// ---- one LSD pass: rank, look-back per digit, staged coalesced scatter ---------------------
+// Warp w of a tile holds the tile's keys w*512 + r*32 + lane (r < kItems), so row-major order
+// is input order and the ranks are stable.
+template <bool kGen>
+__global__ void __launch_bounds__(kBlock, 2)
+onesweep_kernel(const uint64_t* __restrict__ in, ExpandSrc src, uint64_t* __restrict__ out, unsigned long long n,
+                int shift, const unsigned long long* __restrict__ ghist_p, unsigned long long* desc,
+                unsigned* ticket, unsigned epoch, int* err) {
+    __shared__ unsigned s_whist[kWarps][kDigits];
+    __shared__ unsigned s_lstart[kDigits];
+    __shared__ unsigned long long s_base[kDigits];
+    __shared__ uint64_t s_stage[kTile];
     __shared__ int s_tile;
-    __shared__ unsigned long long s_prefix;
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_tile = (int)atomicAdd(ticket, 1u);
+    for (int i = tid; i < kWarps * kDigits; i += kBlock) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const int tile = s_tile;
-    const unsigned long long base = (unsigned long long)tile * kTile + (unsigned long long)threadIdx.x * kItems;
-    unsigned v[kItems];
-    unsigned sum = 0;
+    const unsigned long long base = (unsigned long long)tile * kTile;
+    uint64_t key[kItems];
+    unsigned rank[kItems];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        v[i] = (base + i < n) ? data[base + i] : 0u;
-        sum += v[i];
-    }
-    unsigned total = 0;
-    const unsigned excl = block_exclusive_scan(sum, &total);
-    if (threadIdx.x == 0) {
-        unsigned long long p = 0;
-        if (!look_back(desc, tile, total, &p, err)) p = 0;
-        s_prefix = p;
-    }
-    __syncthreads();
-    unsigned run = (unsigned)s_prefix + excl;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        if (base + i < n) data[base + i] = run;
-        run += v[i];
-    }
-}
-
-// Stable scatter of one LSD pass.  Keys are taken in tile order (round r covers keys
-// [tile*kTile + r*kBlock, +kBlock), lane order within a warp); a key's rank within its tile and
-// digit is the count of equal digits before it in that order, so equal digits keep their
-// relative order (the pass is stable).
-__global__ void __launch_bounds__(kBlock)
-radix_scatter_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, unsigned long long n,
-                     int shift, const unsigned* __restrict__ offsets, int ntiles) {
-    __shared__ unsigned s_run[kDigits];              // running count per digit within the tile
-    __shared__ unsigned s_warp[kBlock / 32][kDigits];
-    const int w = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kDigits; d += kBlock) s_run[d] = 0;
-    const unsigned long long base = (unsigned long long)blockIdx.x * kTile;
     for (int r = 0; r < kItems; ++r) {
-        for (int i = threadIdx.x; i < (kBlock / 32) * kDigits; i += kBlock) (&s_warp[0][0])[i] = 0;
-        __syncthreads();
-        const unsigned long long e = base + (unsigned long long)r * kBlock + threadIdx.x;
-        const bool valid = e < n;
-        const uint64_t key = valid ? in[e] : 0;
-        const unsigned d = valid ? (unsigned)((key >> shift) & (kDigits - 1)) : (unsigned)kDigits;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const unsigned lane_rank = __popc(peers & lanemask_lt());
-        if (valid && lane_rank == 0) s_warp[w][d] = __popc(peers);
-        __syncthreads();
-        // per digit: exclusive prefix over warps, continued from earlier rounds
-        for (int dd = threadIdx.x; dd < kDigits; dd += kBlock) {
-            unsigned run = s_run[dd];
+        const unsigned long long idx = base + (unsigned)(wid * (kItems * 32) + r * 32 + lane);
+        key[r] = idx < n ? (kGen ? gen_candidate(src, idx) : in[idx]) : 0;
+    }
 #pragma unroll
-            for (int ww = 0; ww < kBlock / 32; ++ww) {
-                const unsigned c = s_warp[ww][dd];
-                s_warp[ww][dd] = run;
-                run += c;
-            }
-            s_run[dd] = run;
+    for (int r = 0; r < kItems; ++r) {
+        const unsigned long long idx = base + (unsigned)(wid * (kItems * 32) + r * 32 + lane);
+        const unsigned d = idx < n ? (unsigned)(key[r] >> shift) & (kDigits - 1) : (unsigned)kDigits;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned lt = __popc(peers & lanemask_lt());
+        const unsigned run = d < (unsigned)kDigits ? s_whist[wid][d] : 0u;
+        rank[r] = run + lt;
+        __syncwarp();
+        if (d < (unsigned)kDigits && lt == 0) s_whist[wid][d] = run + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread d: the tile's count of digit d, exclusive over warps in place
+    unsigned cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const unsigned c = s_whist[w][tid];
+        s_whist[w][tid] = cnt;
+        cnt += c;
+    }
+    unsigned tile_total = 0;
+    s_lstart[tid] = block_excl_scan<unsigned>(cnt, &tile_total);
+    unsigned long long all = 0;
+    const unsigned long long goff = block_excl_scan<unsigned long long>(ghist_p[tid], &all);
+    s_base[tid] = goff + look_back(desc + tid, kDigits, tile, cnt, epoch, err);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const unsigned long long idx = base + (unsigned)(wid * (kItems * 32) + r * 32 + lane);
+        if (idx < n) {
+            const unsigned d = (unsigned)(key[r] >> shift) & (kDigits - 1);
+            s_stage[s_lstart[d] + s_whist[wid][d] + rank[r]] = key[r];
         }
-        __syncthreads();
-        if (valid) {
-            const unsigned pos = offsets[(size_t)d * ntiles + blockIdx.x] + s_warp[w][d] + lane_rank;
-            if (pos < n) out[pos] = key;   // always true unless the offset scan failed (error word set)
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    const unsigned tile_n = (unsigned)(n - base < (unsigned long long)kTile ? n - base : (unsigned long long)kTile);
+    for (unsigned i = tid; i < tile_n; i += kBlock) {
+        const uint64_t k = s_stage[i];
+        const unsigned d = (unsigned)(k >> shift) & (kDigits - 1);
+        const unsigned long long pos = s_base[d] + (i - s_lstart[d]);
+        if (pos < n) out[pos] = k;            // always, unless a look-back gave up (error word set)
     }
 }
 
-// ---- unique + merge-path set difference ------------------------------------------------------
-// Number of elements of a among the first `diag` elements of the merge of a and b, where an
-// element of a goes before an equal element of b.
-__device__ __forceinline__ unsigned long long merge_path(const uint64_t* a, unsigned long long na,
-                                                         const uint64_t* b, unsigned long long nb,
-                                                         unsigned long long diag) {
-    unsigned long long lo = diag > nb ? diag - nb : 0;
-    unsigned long long hi = diag < na ? diag : na;
-    while (lo < hi) {
-        const unsigned long long mid = (lo + hi) >> 1;   // candidate count of a-elements
-        // a[mid] goes before b[diag - mid - 1] iff a[mid] <= b[diag - mid - 1]
-        if (a[mid] <= b[diag - mid - 1]) lo = mid + 1;
-        else hi = mid;
+// ---- first of run, set difference and compaction in one pass -------------------------------
+// Lower bound of key in b[j, nb), galloping from j (the keys a thread asks for ascend).
+__device__ __forceinline__ unsigned long long gallop(const uint64_t* __restrict__ b, unsigned long long nb,
+                                                     unsigned long long j, uint64_t key) {
+    if (j >= nb || b[j] >= key) return j;
+    unsigned long long lo = j, step = 1;        // b[lo] < key
+    while (lo + step < nb && b[lo + step] < key) {
+        lo += step;
+        step <<= 1;
     }
-    return lo;
+    unsigned long long hi = lo + step < nb ? lo + step : nb;   // b[hi] >= key or hi = nb
+    while (hi - lo > 1) {
+        const unsigned long long mid = lo + ((hi - lo) >> 1);
+        if (b[mid] < key) lo = mid; else hi = mid;
+    }
+    return hi;
 }
 
-// flags[i] &= (a[i] is absent from b) [and, if first_of_run, a[i] != a[i-1]].  a sorted
-// (duplicates allowed), b sorted.  Each thread walks kItems steps of the merge of a and b.
 __global__ void __launch_bounds__(kBlock)
-setdiff_flags_kernel(const uint64_t* __restrict__ a, unsigned long long na, const uint64_t* __restrict__ b,
-                     unsigned long long nb, unsigned char* __restrict__ flags, int first_of_run, int init) {
-    const unsigned long long total = na + nb;
-    const unsigned long long diag = ((unsigned long long)blockIdx.x * kBlock + threadIdx.x) * kItems;
-    if (diag >= total) return;
-    unsigned long long ai = merge_path(a, na, b, nb, diag);
-    unsigned long long bi = diag - ai;
-    const unsigned long long end = diag + kItems < total ? diag + kItems : total;
-    for (unsigned long long step = diag; step < end; ++step) {
-        if (ai < na && (bi >= nb || a[ai] <= b[bi])) {
-            const uint64_t x = a[ai];
-            bool keep = !(bi < nb && b[bi] == x);
-            if (first_of_run && ai > 0 && a[ai - 1] == x) keep = false;
-            if (init) flags[ai] = keep ? 1 : 0;
-            else if (!keep) flags[ai] = 0;
-            ++ai;
-        } else {
-            ++bi;
-        }
-    }
-}
-
-// ---- compaction ----------------------------------------------------------------------------------
-// out[...] = in[i] for flags[i] != 0, in order; *count = number kept.  Single pass, decoupled
-// look-back over tiles (desc zeroed, ticket zeroed).
-__global__ void __launch_bounds__(kBlock)
-compact_kernel(const uint64_t* __restrict__ in, const unsigned char* __restrict__ flags, unsigned long long n,
-               uint64_t* __restrict__ out, unsigned long long* count, unsigned long long* desc,
-               unsigned* ticket, int ntiles, int* err) {
+unique_diff_kernel(const uint64_t* __restrict__ a, unsigned long long na, const uint64_t* __restrict__ b0,
+                   unsigned long long nb0, const uint64_t* __restrict__ b1, unsigned long long nb1,
+                   int first_of_run, uint64_t* __restrict__ out, unsigned long long* d_count,
+                   unsigned long long* desc, unsigned* ticket, int ntiles, unsigned epoch, int* err) {
+    __shared__ uint64_t s_stage[kTile];
     __shared__ int s_tile;
     __shared__ unsigned long long s_prefix;
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (int)atomicAdd(ticket, 1u);
     __syncthreads();
     const int tile = s_tile;
-    const unsigned long long base = (unsigned long long)tile * kTile + (unsigned long long)threadIdx.x * kItems;
-    unsigned keepmask = 0, cnt = 0;
+    const unsigned long long p0 = (unsigned long long)tile * kTile + (unsigned long long)tid * kItems;
+    uint64_t key[kItems];
+    unsigned keep = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) key[i] = p0 + i < na ? a[p0 + i] : 0;
+    uint64_t prev = (p0 > 0 && p0 - 1 < na) ? a[p0 - 1] : 0;
+    bool has_prev = p0 > 0;
+    unsigned long long j0 = 0, j1 = 0;
+    if (p0 < na) {
+        j0 = gallop(b0, nb0, 0, key[0]);          // galloping from 0 is a binary search
+        j1 = gallop(b1, nb1, 0, key[0]);
+    }
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        const bool k = (base + i < n) && flags[base + i];
-        keepmask |= (unsigned)k << i;
+        if (p0 + i >= na) break;
+        bool k = !(first_of_run && has_prev && prev == key[i]);
+        j0 = gallop(b0, nb0, j0, key[i]);
+        if (j0 < nb0 && b0[j0] == key[i]) k = false;
+        j1 = gallop(b1, nb1, j1, key[i]);
+        if (j1 < nb1 && b1[j1] == key[i]) k = false;
+        keep |= (unsigned)k << i;
         cnt += k;
+        prev = key[i];
+        has_prev = true;
     }
     unsigned total = 0;
-    const unsigned excl = block_exclusive_scan(cnt, &total);
-    if (threadIdx.x == 0) {
-        unsigned long long p = 0;
-        if (!look_back(desc, tile, total, &p, err)) p = 0;
-        s_prefix = p;
-        if (tile == ntiles - 1 && *(volatile int*)err == 0) *count = p + total;
+    const unsigned excl = block_excl_scan<unsigned>(cnt, &total);
+    if (tid == 0) {
+        s_prefix = look_back(desc, 1, tile, total, epoch, err);
+        if (tile == ntiles - 1 && *(volatile int*)err == 0) *d_count = s_prefix + total;
     }
-    __syncthreads();
-    unsigned long long pos = s_prefix + excl;
+    unsigned pos = excl;
 #pragma unroll
     for (int i = 0; i < kItems; ++i)
-        if ((keepmask >> i & 1u) && pos < n) out[pos++] = in[base + i];
+        if (keep >> i & 1u) s_stage[pos++] = key[i];
+    __syncthreads();
+    const unsigned long long o = s_prefix;
+    for (unsigned i = tid; i < total; i += kBlock)
+        if (o + i < na) out[o + i] = s_stage[i];
+}
+
+// ---- key-range chunks of a layer's candidates -----------------------------------------------
+// Append the candidates whose top digit (bits [shift, shift + 8)) lies in [d0, d1) to out, in
+// no particular order (one atomic per warp and step); *count must start at 0.
+__global__ void __launch_bounds__(kBlock)
+expand_filter_kernel(ExpandSrc src, int shift, unsigned d0, unsigned d1, uint64_t* __restrict__ out,
+                     unsigned long long cap, unsigned long long* count, int* err) {
+    const unsigned long long n = src.F * (unsigned long long)src.k;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kBlock;
+    for (unsigned long long w = blockIdx.x * (unsigned long long)kBlock + (threadIdx.x & ~31u); w < n; w += stride) {
+        const unsigned long long i = w + lane;
+        uint64_t t = 0;
+        bool in = false;
+        if (i < n) {
+            t = gen_candidate(src, i);
+            const unsigned d = (unsigned)(t >> shift) & (kDigits - 1);
+            in = d >= d0 && d < d1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (!m) continue;
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(m));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (in) {
+            const unsigned long long pos = b + __popc(m & lanemask_lt());
+            if (pos < cap) out[pos] = t;
+            else atomicExch(err, CG_EDEVICE);
+        }
+    }
+}
+
+__global__ void mask_keys_kernel(uint64_t* keys, unsigned long long n, uint64_t mask) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        keys[i] &= mask;
 }
 
 int tiles_of(unsigned long long n) { return (int)((n + kTile - 1) / kTile); }
+
+int passes_of(int bits) { return (bits + kRadixBits - 1) / kRadixBits; }
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
 // ---- host-side launchers ---------------------------------------------------------------------------
 
+// Layout: keys_tmp | error word (256 B) | digit histograms | tickets (256 B) | descriptors.
+// A sort clears histograms, tickets and descriptors with one memset (never the error word,
+// which the caller clears once per operation and reads at its end).
 size_t sort_scratch_bytes(unsigned long long n) {
     const unsigned long long nt = (unsigned long long)tiles_of(n ? n : 1);
-    const unsigned long long hist = (unsigned long long)kDigits * nt;           // u32
-    const unsigned long long scan_tiles = (hist + kTile - 1) / kTile + 1;
-    size_t b = 0;
-    b += ((n * 8 + 255) / 256) * 256;                       // ping-pong keys
-    b += ((hist * 4 + 255) / 256) * 256;                    // histograms / offsets
-    b += ((scan_tiles * 8 + 255) / 256) * 256;              // scan descriptors
-    b += ((nt * 8 + 255) / 256) * 256;                      // compaction descriptors
-    b += ((n + 255) / 256) * 256;                           // flags
-    b += 256;                                               // tickets, error word
-    return b;
+    return al(n * 8) + 256 + al(sizeof(unsigned long long) * kSortMaxPasses * kDigits) + 256 +
+           al(nt * kDigits * 8);
 }
 
 SortScratch carve_sort_scratch(void* scratch, unsigned long long n) {
     SortScratch s{};
     char* p = static_cast<char*>(scratch);
     const unsigned long long nt = (unsigned long long)tiles_of(n ? n : 1);
-    const unsigned long long hist = (unsigned long long)kDigits * nt;
-    const unsigned long long scan_tiles = (hist + kTile - 1) / kTile + 1;
-    auto take = [&](size_t bytes) { char* r = p; p += ((bytes + 255) / 256) * 256; return r; };
-    s.keys_tmp = reinterpret_cast<uint64_t*>(take(n * 8));
-    s.hist = reinterpret_cast<unsigned*>(take(hist * 4));
-    s.scan_desc = reinterpret_cast<unsigned long long*>(take(scan_tiles * 8));
-    s.compact_desc = reinterpret_cast<unsigned long long*>(take(nt * 8));
-    s.flags = reinterpret_cast<unsigned char*>(take(n));
-    char* small = take(256);
-    s.tickets = reinterpret_cast<unsigned*>(small);            // [0] scan, [1] compaction
-    s.err = reinterpret_cast<int*>(small + 64);
+    s.keys_tmp = reinterpret_cast<uint64_t*>(p);
+    p += al(n * 8);
+    s.err = reinterpret_cast<int*>(p);
+    p += 256;
+    s.ghist = reinterpret_cast<unsigned long long*>(p);
+    p += al(sizeof(unsigned long long) * kSortMaxPasses * kDigits);
+    s.ctl = reinterpret_cast<unsigned*>(p);           // tile tickets: [p] pass p, [15] compaction
+    p += 256;
+    s.desc = reinterpret_cast<unsigned long long*>(p);
     s.n = n;
+    s.reset_bytes = al(sizeof(unsigned long long) * kSortMaxPasses * kDigits) + 256 + al(nt * kDigits * 8);
     return s;
 }
 
@@ -354,59 +398,115 @@ cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, un
     return cudaGetLastError();
 }
 
-// Sort keys[0, n) ascending on their low `bits` bits (higher bits must be zero), in place; the
-// number of 8-bit passes is ceil(bits / 8), an odd count ends with one extra copy.
+namespace {
+
+// The passes of one sort.  Input: `in` keys, or the candidates of src (gen).  Pass p writes
+// bufs[(P - 1 - p) & 1], so the last pass writes bufs[0].  The error word and the descriptors
+// are cleared first (one memset); the caller zeroes nothing.
+cudaError_t radix_passes(const uint64_t* in, const ExpandSrc* src, unsigned long long n, int bits,
+                         uint64_t* const bufs[2], const SortScratch& s, cudaStream_t st) {
+    const int P = passes_of(bits < 1 ? 1 : bits);
+    const int nt = tiles_of(n);
+    const size_t reset = al(sizeof(unsigned long long) * kSortMaxPasses * kDigits) + 256 + al((size_t)nt * kDigits * 8);
+    cudaError_t e = cudaMemsetAsync(s.ghist, 0, reset, st);
+    if (e != cudaSuccess) return e;
+    const ExpandSrc none{};
+    unsigned long long hb = (n + kBlock - 1) / kBlock;
+    if (hb > 152ull * 4) hb = 152ull * 4;
+    if (src) hist_all_kernel<true><<<(unsigned)hb, kBlock, 0, st>>>(nullptr, *src, n, P, s.ghist);
+    else hist_all_kernel<false><<<(unsigned)hb, kBlock, 0, st>>>(in, none, n, P, s.ghist);
+    const uint64_t* cur = in;
+    for (int p = 0; p < P; ++p) {
+        uint64_t* dst = bufs[(P - 1 - p) & 1];
+        if (p == 0 && src)
+            onesweep_kernel<true><<<nt, kBlock, 0, st>>>(nullptr, *src, dst, n, kRadixBits * p,
+                                                         s.ghist + p * kDigits, s.desc, s.ctl + p,
+                                                         (unsigned)(p + 1), s.err);
+        else
+            onesweep_kernel<false><<<nt, kBlock, 0, st>>>(cur, none, dst, n, kRadixBits * p,
+                                                          s.ghist + p * kDigits, s.desc, s.ctl + p,
+                                                          (unsigned)(p + 1), s.err);
+        cur = dst;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Sort keys[0, n) ascending on their low `bits` bits (higher bits must be zero), in place; an
+// odd number of 8-bit passes ends with one copy back.
 cudaError_t launch_radix_sort(uint64_t* keys, unsigned long long n, int bits, const SortScratch& s,
                               cudaStream_t st) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (n <= 1) return cudaSuccess;
-    const int nt = tiles_of(n);
-    const unsigned long long hist_n = (unsigned long long)kDigits * nt;
-    const int scan_tiles = tiles_of(hist_n);
-    uint64_t* src = keys;
-    uint64_t* dst = s.keys_tmp;
-    const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    cudaError_t e = cudaSuccess;
-    for (int p = 0; p < passes && e == cudaSuccess; ++p) {
-        const int shift = p * kRadixBits;
-        radix_hist_kernel<<<nt, kBlock, 0, st>>>(src, n, shift, s.hist, nt);
-        if ((e = cudaMemsetAsync(s.scan_desc, 0, (size_t)scan_tiles * 8, st)) != cudaSuccess) break;
-        if ((e = cudaMemsetAsync(s.tickets, 0, 4, st)) != cudaSuccess) break;
-        scan_u32_kernel<<<scan_tiles, kBlock, 0, st>>>(s.hist, hist_n, s.scan_desc, s.tickets, s.err);
-        radix_scatter_kernel<<<nt, kBlock, 0, st>>>(src, dst, n, shift, s.hist, nt);
-        e = cudaGetLastError();
-        uint64_t* t = src; src = dst; dst = t;
-    }
-    if (e == cudaSuccess && src != keys)
-        e = cudaMemcpyAsync(keys, src, n * 8, cudaMemcpyDeviceToDevice, st);
+    const int P = passes_of(bits);
+    uint64_t* bufs[2];
+    if (P % 2 == 0) { bufs[0] = keys; bufs[1] = s.keys_tmp; }
+    else { bufs[0] = s.keys_tmp; bufs[1] = keys; }
+    cudaError_t e = radix_passes(keys, nullptr, n, bits, bufs, s, st);
+    if (e == cudaSuccess && P % 2 == 1)
+        e = cudaMemcpyAsync(keys, s.keys_tmp, n * 8, cudaMemcpyDeviceToDevice, st);
     return e;
 }
 
-// flags[i] = a[i] is the first of its run and absent from every b_j; then compaction of a into
-// out, count into *d_count.  a sorted; each b_j sorted.
+cudaError_t launch_expand_sort(const ExpandSrc& src, uint64_t* out, int bits, const SortScratch& s,
+                               cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    const unsigned long long n = src.F * (unsigned long long)src.k;
+    if (n == 0) return cudaSuccess;
+    uint64_t* bufs[2] = {out, s.keys_tmp};
+    return radix_passes(nullptr, &src, n, bits, bufs, s, st);
+}
+
+// out = keys of sorted a that are first of their run and absent from every sorted b_j,
+// compacted in order; *d_count = their number.
 cudaError_t launch_unique_difference(const uint64_t* a, unsigned long long na, const uint64_t* const* bs,
                                      const unsigned long long* nbs, int nb_sets, uint64_t* out,
                                      unsigned long long* d_count, const SortScratch& s, cudaStream_t st) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (na == 0) return cudaMemsetAsync(d_count, 0, 8, st);
-    cudaError_t e = cudaSuccess;
-    for (int j = 0; j < (nb_sets > 0 ? nb_sets : 1) && e == cudaSuccess; ++j) {
-        const uint64_t* b = nb_sets > 0 ? bs[j] : a;
-        const unsigned long long nb = nb_sets > 0 ? nbs[j] : 0;
-        const unsigned long long total = na + nb;
-        const unsigned long long threads = (total + kItems - 1) / kItems;
-        const unsigned blocks = (unsigned)((threads + kBlock - 1) / kBlock);
-        setdiff_flags_kernel<<<blocks, kBlock, 0, st>>>(a, na, b, nb, s.flags, j == 0 ? 1 : 0,
-                                                        j == 0 ? 1 : 0);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return e;
     const int nt = tiles_of(na);
-    if ((e = cudaMemsetAsync(s.compact_desc, 0, (size_t)nt * 8, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(s.tickets + 1, 0, 4, st)) != cudaSuccess) return e;
-    compact_kernel<<<nt, kBlock, 0, st>>>(a, s.flags, na, out, d_count, s.compact_desc, s.tickets + 1,
-                                          nt, s.err);
+    // its own ticket and descriptors (epoch 15): clear the tickets and one descriptor per tile
+    cudaError_t e = cudaMemsetAsync(s.ctl, 0, 256 + al((size_t)nt * 8), st);
+    if (e != cudaSuccess) return e;
+    const uint64_t* b0 = nb_sets > 0 ? bs[0] : a;
+    const uint64_t* b1 = nb_sets > 1 ? bs[1] : a;
+    const unsigned long long n0 = nb_sets > 0 ? nbs[0] : 0, n1 = nb_sets > 1 ? nbs[1] : 0;
+    unique_diff_kernel<<<nt, kBlock, 0, st>>>(a, na, b0, n0, b1, n1, 1, out, d_count, s.desc, s.ctl + 15,
+                                              nt, 15u, s.err);
     return cudaGetLastError();
 }
+
+cudaError_t launch_candidate_hist(const ExpandSrc& src, int bits, const SortScratch& s, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    const unsigned long long n = src.F * (unsigned long long)src.k;
+    cudaError_t e = cudaMemsetAsync(s.ghist, 0, sizeof(unsigned long long) * kSortMaxPasses * kDigits, st);
+    if (e != cudaSuccess || n == 0) return e;
+    unsigned long long hb = (n + kBlock - 1) / kBlock;
+    if (hb > 152ull * 4) hb = 152ull * 4;
+    hist_all_kernel<true><<<(unsigned)hb, kBlock, 0, st>>>(nullptr, src, n, passes_of(bits), s.ghist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_filter(const ExpandSrc& src, int shift, unsigned d0, unsigned d1, uint64_t* out,
+                                 unsigned long long cap, unsigned long long* d_count, int* d_err,
+                                 cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    cudaError_t e = cudaMemsetAsync(d_count, 0, 8, st);
+    if (e != cudaSuccess || src.F == 0) return e;
+    expand_filter_kernel<<<152 * 8, kBlock, 0, st>>>(src, shift, d0, d1, out, cap, d_count, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_keys(uint64_t* keys, unsigned long long n, uint64_t mask, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    if (n == 0) return cudaSuccess;
+    unsigned long long blocks = (n + 255) / 256;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    mask_keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys, n, mask);
+    return cudaGetLastError();
+}
+
+int sort_passes(int bits) { return passes_of(bits < 1 ? 1 : bits); }
 
 }  // namespace cg

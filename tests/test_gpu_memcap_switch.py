@@ -53,16 +53,21 @@ def test_binary_coset_switches_and_completes(cg):
 
 
 def test_sorted_step_truncates_exactly(cg):
-    # at 1300 KiB the switch happens but the sorted step itself runs out later: the reported
-    # layers are an exact prefix
+    # at 1000 KiB the switch happens but the sorted step itself runs out later (the two largest
+    # layers and the next one's buffer leave no room for candidates): an exact prefix
     gens = w.lrx(9)
     want, _ = oracle.growth(9, gens)
-    with cg.Growth(9, gens, max_radius=40, mem_cap=1300 << 10) as g:
+    with cg.Growth(9, gens, max_radius=40, mem_cap=1000 << 10) as g:
         r = g.run()
         st = g.stats()
     assert r.status == 2                      # CG_TRUNC_MEMCAP
     assert 1 < len(r.layers) < len(want) and r.layers == want[:len(r.layers)]
     assert st["switched_to_sort"] == 1
+    # at 1600 KiB the sorted step completes: its largest steps (112,548 candidates, 1.9 MB at
+    # once) run in key-range chunks beside the three layers
+    with cg.Growth(9, gens, max_radius=40, mem_cap=1600 << 10) as g:
+        r = g.run()
+        assert r.status == 0 and r.layers == want and g.stats()["switched_to_sort"] == 1
 
 
 def test_directed_set_keeps_the_truncation(cg):

@@ -265,7 +265,7 @@ def test_batch_with_hash_visited_sets(cg):
     assert res[2].layers == oracle.growth(7, w.lx(7))[0]
 
 
-@pytest.mark.parametrize("strategy", ["bitmap", "hash"])
+@pytest.mark.parametrize("strategy", ["bitmap", "hash", "sort"])
 def test_config3_s14_pancake_full_size(cg, strategy):
     # Config 3 at full size: layers 0..10 (2.6e9 states in the last one) against oracle B.
     job = w.config_s14_pancake()

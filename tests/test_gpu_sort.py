@@ -135,3 +135,19 @@ def test_sort_strategy_limits_and_last_layer(cg):
     want = golden("s11_lrx_growth")
     r = cg.growth(11, w.lrx(11), strategy="sort", mem_cap=48 << 20)
     assert r.status == 2 and r.layers == want[:len(r.layers)]
+
+
+def test_sort_strategy_key_range_chunks(cg):
+    # 200 MB holds the three largest layers of S_11 LRX but not their 9.15M candidates at once:
+    # the large steps run in key-range chunks (top-digit histogram, then one sort per range)
+    r = cg.growth(11, w.lrx(11), strategy="sort", mem_cap=200 << 20)
+    assert r.status == 0 and r.layers == golden("s11_lrx_growth")
+    r = cg.growth(11, w.lrx(11), strategy="sort", mem_cap=120 << 20)
+    want = golden("s11_lrx_growth")
+    assert r.layers == want[:len(r.layers)] and (r.status == 0 or r.status == 2)
+
+
+def test_sort_strategy_s12_pancake_whole(cg):
+    # all 12! states through the sorted two-layer step (11 generators), against oracle B
+    r = cg.growth(12, w.pancake(12), strategy="sort")
+    assert r.status == 0 and r.layers == golden("s12_pancake_growth_b")
