@@ -273,39 +273,55 @@ __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words
         if ((vmask >> i & 1u) && res[i] == 0) res[i] = (old[i] & bit[i]) ? 0 : 1;
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_ull(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_ull(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
 // Arrival half of a grid barrier whose last arriving block does some work before releasing
-// the others (cooperative launch: all blocks co-resident).  Returns 1 in every thread of the
-// block that arrived last (it must call grid_release after its work), 0 in the other blocks
-// once the last block has released them, -1 on error (timeout or an error word set by
-// another block: the caller returns from the kernel).  `word` receives the barrier word: for
-// the last block the one it arrived on (pass it to grid_release), for the others the one the
-// release wrote, whose payload is word >> kGenBits.
-__device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns, unsigned long long& word) {
+// the others (cooperative launch: all blocks co-resident).  `gen` is the number of barriers
+// this block has passed in the launch (every block passes the same ones).  Returns 1 in every
+// thread of the block that arrived last (it must call grid_release after its work), 0 in the
+// other blocks once the last block has released them, -1 on error (timeout or an error word
+// set by another block: the caller returns from the kernel).  `word` receives the barrier word:
+// for the last block the one it arrived on (pass it to grid_release), for the others the one
+// the release wrote, whose payload is word >> kGenBits.
+// Ordering: every arrival is an acquire-release atomic (the block's writes before it, ordered
+// by the block's own barrier, are visible to whoever observes it later, and the last arrival
+// acquires everything released before), and the waiters' poll of the barrier word is an
+// acquire of the closing block's work.
+__device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns, unsigned long long& word,
+                                           unsigned gen) {
     __shared__ int s_state;
     __shared__ unsigned long long s_word;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned long long* vword = &ctl->bar_word;
-        const unsigned long long w0 = *vword;
-        const unsigned gen = (unsigned)(w0 & kGenMask);
-        __threadfence();
+        gen &= (unsigned)kGenMask;
         const unsigned g = blockIdx.x % kBarGroups;
         const unsigned gsize = (gridDim.x - g + kBarGroups - 1) / kBarGroups;
         const unsigned ngroups = gridDim.x < (unsigned)kBarGroups ? gridDim.x : (unsigned)kBarGroups;
         int state = 0;
-        unsigned long long w = w0;
+        unsigned long long w = gen;
         // The counters only grow (zeroed before each launch): barrier `gen` is complete in a
         // group when its counter reaches gsize * (gen + 1), so nothing is reset on the way.
-        if (atomicAdd(&ctl->group[g].count, 1u) == gsize * (gen + 1) - 1) {
-            if (atomicAdd(&ctl->bar_count, 1u) == ngroups * (gen + 1) - 1) {
-                __threadfence();
-                state = 1;
-            }
+        if (atom_add_acq_rel(&ctl->group[g].count, 1u) == gsize * (gen + 1) - 1) {
+            if (atom_add_acq_rel(&ctl->bar_count, 1u) == ngroups * (gen + 1) - 1) state = 1;
         }
         if (state == 0) {
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
-            while (((w = *vword) & kGenMask) == gen) {
+            while (((w = ld_acquire_ull(&ctl->bar_word)) & kGenMask) == gen) {
                 if ((++spins & 63u) == 0) {
                     if (*(volatile int*)&ctl->err != 0) { state = -1; break; }
                     if (globaltimer_ns() - t0 > timeout_ns) {
@@ -316,8 +332,6 @@ __device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns, unsign
                 }
                 __nanosleep(spins < 64 ? 32 : 256);
             }
-            __threadfence();
-            if (state == 0 && *(volatile int*)&ctl->err != 0) state = -1;
         }
         s_state = state;
         s_word = w;
@@ -332,9 +346,8 @@ __device__ __forceinline__ int grid_arrive(Ctl* ctl, uint64_t timeout_ns, unsign
 __device__ __forceinline__ void grid_release(Ctl* ctl, unsigned long long word, unsigned long long payload) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned long long gen = ((word & kGenMask) + 1) & kGenMask;
-        atomicExch(&ctl->bar_word, gen | (payload << kGenBits));
+        st_release_ull(&ctl->bar_word, gen | (payload << kGenBits));
     }
 }
 

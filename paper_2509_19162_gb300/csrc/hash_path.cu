@@ -333,9 +333,8 @@ __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* 
         *next_fresh = units ? tail - hi : 0;
         *next_lo = hi;
         *next_hi = tail;
-        // After the caller's __syncthreads, this fence makes the block's new states and the
-        // job's new frontier visible device-wide before the next round reads them via L2.
-        __threadfence();
+        // The release of the barrier (grid_release) makes these writes visible to the blocks
+        // it wakes; rounds this block runs alone see them after its own __syncthreads.
     }
     __syncthreads();
 }
@@ -557,6 +556,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         s_hi = running ? ld_relaxed_ull(&jobs[0].hi) : s_lo;
     }
 
+    unsigned nbar = 0;                      // grid barriers this block has passed
     for (int round = 0; round < max_rounds; ++round) {
         if (threadIdx.x == 0) {
             s_total = kMulti ? ld_relaxed_ull(&ctl->total_units) : (s_hi - s_lo + 31) >> 5;
@@ -637,7 +637,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         // One barrier per round: the last block to finish the round closes it (layer counts,
         // stop tests, next round's work layout) and then releases the others.
         unsigned long long word = 0;
-        const int arrive = grid_arrive(ctl, timeout_ns, word);
+        const int arrive = grid_arrive(ctl, timeout_ns, word, nbar++);
         if (arrive < 0) return;
         if (arrive == 1) {
             if (!kMulti) {

@@ -199,6 +199,7 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
     unsigned* lbuf = s_list[wid];
     const unsigned long long nwarps = (unsigned long long)gridDim.x * kSweepWarps;
 
+    unsigned nbar = 0;                      // grid barriers this block has passed
     for (int round = 0; round < max_rounds; ++round) {
         if (ld_relaxed_int(&D.status) != kRunning) break;
         const int r = ld_relaxed_int(&D.radius);
@@ -384,7 +385,7 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
         if (threadIdx.x == 0 && s_fresh) atomicAdd(&D.fresh, s_fresh);
 
         unsigned long long word = 0;
-        const int arrive = grid_arrive(ctl, timeout_ns, word);
+        const int arrive = grid_arrive(ctl, timeout_ns, word, nbar++);
         if (arrive < 0) return;
         if (arrive == 1) {
             if (threadIdx.x == 0) sweep_close(D, ctl);

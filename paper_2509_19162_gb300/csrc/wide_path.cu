@@ -215,6 +215,7 @@ wide_grow_kernel(WideDev* J, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
     }
     const int lane = threadIdx.x & 31;
     Key128* buf = s_stage[threadIdx.x >> 5];
+    unsigned nbar = 0;                      // grid barriers this block has passed
     for (int round = 0; round < max_rounds; ++round) {
         if (threadIdx.x == 0) {
             s_run = ld_relaxed_int(&J->status) == kRunning;
@@ -239,7 +240,7 @@ wide_grow_kernel(WideDev* J, Ctl* ctl, int max_rounds, uint64_t timeout_ns) {
         }
         wide_flush(buf, cnt, J, lane);
         unsigned long long word = 0;
-        const int arrive = grid_arrive(ctl, timeout_ns, word);
+        const int arrive = grid_arrive(ctl, timeout_ns, word, nbar++);
         if (arrive < 0) return;
         if (arrive == 1) {
             if (threadIdx.x == 0) wide_close(J, ctl);
