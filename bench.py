@@ -514,13 +514,15 @@ def measure_batch(cg, spec, stream, flush, steps, warmup, autotune=True, tune_ta
             "kernel_ms": kernel_ms, "launches": launches, "variant": variant, "tuned": tuned}
 
 
-def one_at_a_time(cg, jobs, stream, mem_cap=0):
+def one_at_a_time(cg, jobs, stream, mem_cap=0, strategies=None):
     """Jobs run one after another through growth() on the same GPU: (layers, seconds)."""
     import torch
+    strategies = strategies or ["auto"] * len(jobs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out = [cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=mem_cap, stream=stream).layers
-           for j in jobs]
+    out = [cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=mem_cap, strategy=s,
+                     stream=stream).layers
+           for j, s in zip(jobs, strategies)]
     return out, time.perf_counter() - t0
 
 
@@ -614,7 +616,7 @@ def run_batch(args):
 SERVE_BUDGET = 160 << 30
 
 
-def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=4, job_mem=0, lam_sample=200):
+def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=8, job_mem=0, lam_sample=200):
     """Serve `jobs` at multiples of the one-at-a-time capacity lambda_1 (measured first on the
     same GPU, each job alone with the same per-job share).  job_mem = 0: the server's default
     share of the 160 GiB budget (budget / 64).  Returns (lambda_1, [one summary per rate])."""
@@ -624,8 +626,11 @@ def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=4, job_m
     plans = [Server.predict(j.n, j.gens, j.inverse_closed, j.max_radius, job_mem_cap=share) for j in jobs]
     over = [i for i, p in enumerate(plans) if p["granted"] < p["states"]]
     sample = jobs[:lam_sample]
-    one_at_a_time(cg, sample[:10], stream, mem_cap=share)
-    _, one_s = one_at_a_time(cg, sample, stream, mem_cap=share)
+    # each job alone with the memory and the visited set the server gives it (no hand-off to
+    # the sorted step, which the server does not make either)
+    strat = [p["visited"] for p in plans[:lam_sample]]
+    one_at_a_time(cg, sample[:10], stream, mem_cap=share, strategies=strat[:10])
+    alone, one_s = one_at_a_time(cg, sample, stream, mem_cap=share, strategies=strat)
     lam1 = len(sample) / one_s
     out = []
     for mult in rates:
@@ -639,6 +644,10 @@ def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=4, job_m
             clocks = sampler.stop()
         statuses = [r.status for r in rep.results]
         memcap_ended = [i for i, st in enumerate(statuses) if st == 2]
+        for a, r in zip(alone, rep.results):           # the same growth alone and in the mix
+            m = min(len(a), len(r.layers))
+            if a[:m] != r.layers[:m]:
+                raise RuntimeError("a served job's layers differ from the same job grown alone")
         out.append({
             "rate": f"{mult:g} x one-at-a-time capacity", "arrival_rate_jobs_per_s": lam,
             "jobs_per_s": rep.jobs_per_s, "makespan_s": rep.makespan_s,
@@ -761,7 +770,7 @@ def main():
     ap.add_argument("--serve-job-mem", type=int, default=0,
                     help="per-job device memory share, MiB (0: the server default, budget / 64)")
     ap.add_argument("--serve-slots", type=int, default=512)
-    ap.add_argument("--serve-rounds", type=int, default=4)
+    ap.add_argument("--serve-rounds", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

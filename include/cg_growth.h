@@ -289,7 +289,10 @@ int cg_batch_destroy(cg_batch_t b);
  * inverse-closed, k^r otherwise, and never more than the group order), stored with the cheaper
  * visited set (hash table, or the rank bitmap for n <= 14), capped at job_mem_cap bytes per job,
  * the job's share of the budget (a job that needs more stops with CG_TRUNC_MEMCAP; its reported
- * layers are exact).  Each cg_server_step admits what fits, then runs up to rounds_per_step layer steps of
+ * layers are exact).  A job predicted to reach at least 2^24 states fills the GPU by itself: when
+ * it reaches the head of the queue, cg_server_step grows it alone with the single-job kernels
+ * (same visited set and share, so the same layers) before the batched launch.  Each
+ * cg_server_step admits what fits, then runs up to rounds_per_step layer steps of
  * every admitted job in one persistent launch on the caller's stream (jobs' states stay on the
  * device between steps), waits for it, and retires the jobs that ended, releasing their slot
  * and memory.  Results are the same as cg_growth_run's for the same job with the same memory.
@@ -308,7 +311,8 @@ int cg_batch_destroy(cg_batch_t b);
  *                      under the per-job share job_mem_cap (> 0): *states_out the predicted
  *                      states up to its radius cap, *granted_out the states it may store (less
  *                      than the prediction: the job may stop with CG_TRUNC_MEMCAP), *bytes_out
- *                      the device bytes it is admitted with.  Any output may be NULL.
+ *                      the device bytes it is admitted with, *visited_out its visited set
+ *                      (CG_STRATEGY_HASH or CG_STRATEGY_BITMAP).  Any output may be NULL.
  *                      Errors: CG_EINVAL, CG_ENOTCLOSED.
  */
 typedef struct cg_server* cg_server_t;
@@ -318,7 +322,7 @@ int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inver
                      int max_radius, uint64_t* job_id_out);
 int cg_server_predict(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
                       uint64_t job_mem_cap, uint64_t* states_out, uint64_t* granted_out,
-                      uint64_t* bytes_out);
+                      uint64_t* bytes_out, int* visited_out);
 int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finished_out);
 int cg_server_finished(cg_server_t s, uint64_t* ids_out, int cap, int* count_out);
 int cg_server_result(cg_server_t s, uint64_t job_id, uint64_t* layers_out, int cap,

@@ -86,7 +86,7 @@ SIGNATURES = {
                                         ctypes.POINTER(_vp)]),
     "cg_server_submit": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int, _u64p]),
     "cg_server_predict": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_uint64, _u64p, _u64p, _u64p]),
+                                         ctypes.c_uint64, _u64p, _u64p, _u64p, _ip]),
     "cg_server_step": (ctypes.c_int, [_vp, _vp, _ip, _ip]),
     "cg_server_finished": (ctypes.c_int, [_vp, _u64p, ctypes.c_int, _ip]),
     "cg_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, _u64p, ctypes.c_int, _ip, _ip]),

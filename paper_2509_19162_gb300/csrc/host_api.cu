@@ -2217,6 +2217,10 @@ int cg_batch_destroy(cg_batch_t b) {
 namespace {
 
 constexpr int kSrvMaxGens = 128;     // generators per job
+// A job predicted to reach at least this many states fills the GPU by itself: it is grown
+// alone by the single-job kernels (the fastest for it) when it reaches the head of the queue,
+// and the smaller jobs around it are batched.
+constexpr uint64_t kSrvSoloStates = 1ull << 24;
 constexpr int kSrvLayers = 4096;     // layer sizes kept per job (more: CG_TRUNC_RADIUS)
 
 // Upper bound on the states a job visits up to its radius cap: sphere r of a graph of
@@ -2276,6 +2280,9 @@ struct cg_server {
         std::vector<GenSM> gsm;
         uint64_t order = 1, cap = 1, bytes = 0, visited_words = 0;
         int mode = cg::kVisitHash;
+        bool solo = false;                 // predicted to fill the GPU: grown alone
+        int inverse_closed = 0;
+        std::vector<uint8_t> rows;         // distinct rows, k * n bytes (for a solo growth)
     };
     struct Slot {
         bool used = false;
@@ -2334,6 +2341,7 @@ int server_admit(cg_server* s, cudaStream_t st) {
             if (!s->slots[i].used) { free_slot = i; break; }
         if (free_slot < 0) break;
         cg_server::Job& q = s->queue.front();
+        if (q.solo) break;                      // grown alone by cg_server_step, in order
         if (s->used + q.bytes > s->budget && s->active > 0) break;
         char* mem = (char*)dev_alloc(q.bytes, st);
         if (!mem) {
@@ -2374,6 +2382,32 @@ int server_admit(cg_server* s, cudaStream_t st) {
                                  cudaMemcpyHostToDevice, st)))
             return cuda_rc(e);
     }
+    return CG_OK;
+}
+
+// Grow the solo job at the head of the queue alone with the single-job path: the same visited
+// set and per-job share the batched launch would give it (so the same layers), no hand-off to
+// the sorted step.  Its result joins the finished list.
+int server_run_solo(cg_server* s, cudaStream_t st) {
+    cg_server::Job J = std::move(s->queue.front());
+    s->queue.pop_front();
+    cg_growth_t g = nullptr;
+    // a served job keeps at most kSrvLayers layers, as in the batched launch
+    const int rad = (J.max_radius < 0 || J.max_radius > kSrvLayers - 1) ? kSrvLayers - 1 : J.max_radius;
+    int rc = cg_growth_create(J.n, J.k, J.rows.data(), J.inverse_closed, rad, s->job_cap_bytes, &g);
+    if (rc) return rc;
+    rc = cg_growth_set_option(g, CG_OPT_STRATEGY,
+                              J.mode == cg::kVisitBitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH);
+    std::vector<uint64_t> layers(kSrvLayers);
+    int nl = 0;
+    if (rc == CG_OK) rc = cg_growth_run(g, st, layers.data(), kSrvLayers, &nl);
+    cg_growth_destroy(g);
+    if (rc < 0) return rc;
+    cg_server::Result R;
+    R.layers.assign(layers.begin(), layers.begin() + nl);
+    R.status = rc;
+    s->results[J.id] = std::move(R);
+    s->finished.push_back(J.id);
     return CG_OK;
 }
 
@@ -2419,6 +2453,9 @@ int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inver
     J.visited_words = P.visited_words;
     J.cap = P.cap;
     J.bytes = P.bytes;
+    J.solo = P.want >= kSrvSoloStates;
+    J.inverse_closed = inverse_closed ? 1 : 0;
+    J.rows = flat;
     if (J.k == 0 || J.max_radius == 0) {       // only the identity: done at once
         cg_server::Result R;
         R.layers = {1};
@@ -2434,7 +2471,7 @@ int cg_server_submit(cg_server_t s, int n, int k, const uint8_t* gens, int inver
 
 int cg_server_predict(int n, int k, const uint8_t* gens, int inverse_closed, int max_radius,
                       uint64_t job_mem_cap, uint64_t* states_out, uint64_t* granted_out,
-                      uint64_t* bytes_out) {
+                      uint64_t* bytes_out, int* visited_out) {
     int rc = validate(n, k, gens);
     if (rc) return rc;
     if (job_mem_cap == 0) return CG_EINVAL;
@@ -2448,6 +2485,7 @@ int cg_server_predict(int n, int k, const uint8_t* gens, int inverse_closed, int
     if (states_out) *states_out = P.want;
     if (granted_out) *granted_out = P.cap;
     if (bytes_out) *bytes_out = P.bytes;
+    if (visited_out) *visited_out = P.mode == cg::kVisitBitmap ? CG_STRATEGY_BITMAP : CG_STRATEGY_HASH;
     return CG_OK;
 }
 
@@ -2457,6 +2495,9 @@ int cg_server_step(cg_server_t s, void* cuda_stream, int* active_out, int* finis
     int rc = server_init_device(s, st);
     if (rc) return rc;
     const size_t finished_before = s->finished.size();
+    if (!s->queue.empty() && s->queue.front().solo) {
+        if ((rc = server_run_solo(s, st))) return rc;
+    }
     if ((rc = server_admit(s, st))) return rc;
     if (s->active > 0) {
         int maxk = 1;

@@ -44,17 +44,19 @@ class Server:
     def predict(n: int, gens: Sequence[Sequence[int]], inverse_closed: Optional[bool] = None,
                 max_radius: int = -1, job_mem_cap: int = 160 << 24) -> Dict[str, int]:
         """Admission plan of a job under the per-job share job_mem_cap (bytes; the server's default
-        share is its budget / 64): predicted states up to the radius cap, states granted, and the
-        device bytes it is admitted with.  Host only."""
+        share is its budget / 64): predicted states up to the radius cap, states granted, the
+        device bytes it is admitted with, and its visited set ("hash" or "bitmap").  Host only."""
         g = _gens_bytes(n, gens)
         if inverse_closed is None:
             inverse_closed = _is_inverse_closed(gens)
         st, gr, by = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        vis = ctypes.c_int(0)
         _cg.check(_cg.cg_server_predict(int(n), int(g.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                         int(bool(inverse_closed)), int(max_radius), int(job_mem_cap),
-                                        ctypes.byref(st), ctypes.byref(gr), ctypes.byref(by)),
+                                        ctypes.byref(st), ctypes.byref(gr), ctypes.byref(by), ctypes.byref(vis)),
                   "cg_server_predict")
-        return {"states": int(st.value), "granted": int(gr.value), "bytes": int(by.value)}
+        return {"states": int(st.value), "granted": int(gr.value), "bytes": int(by.value),
+                "visited": "bitmap" if vis.value == _cg.CG_STRATEGY_BITMAP else "hash"}
 
     def step(self, stream=None):
         a = ctypes.c_int(0)

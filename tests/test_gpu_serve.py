@@ -56,7 +56,7 @@ def test_budget_limits_admission(cg):
 
 def test_late_arrivals_join_running_jobs(cg):
     from paper_2509_19162_gb300.serve import Server
-    big = (11, w.lrx(11), True, -1)
+    big = (9, w.lrx(9), True, -1)                   # 36 layers: 18 steps of 2 rounds
     with Server(max_slots=8, rounds_per_step=2) as s:
         a = s.submit(*big[:2], big[2], big[3])
         s.step()                                    # a is on the GPU
@@ -70,7 +70,28 @@ def test_late_arrivals_join_running_jobs(cg):
                 done[jid] = s.result(jid)
         assert seen_both
         assert done[b].layers == oracle.growth(8, w.coxeter(8))[0]
-        assert sum(done[a].layers) == 39916800 and done[a].status == 0
+        assert done[a].layers == oracle.growth(9, w.lrx(9))[0] and done[a].status == 0
+
+
+def test_jobs_that_fill_the_gpu_are_grown_alone(cg):
+    # S_11 LRX (39.9M states predicted) is grown by the single-job kernels when it reaches the
+    # head of the queue; the small jobs queued around it are batched, in order
+    import os
+    from paper_2509_19162_gb300.serve import Server
+    golden = os.path.join(os.path.dirname(__file__), "golden", "s11_lrx_growth.txt")
+    want = [int(l.split()[1]) for l in open(golden) if not l.startswith("#")]
+    assert Server.predict(11, w.lrx(11), True, -1)["states"] >= 1 << 24
+    with Server(max_slots=8, rounds_per_step=4) as s:
+        ids = [s.submit(8, w.coxeter(8), True, -1), s.submit(11, w.lrx(11), True, -1),
+               s.submit(7, w.pancake(7), True, -1)]
+        done = {}
+        while len(done) < 3:
+            s.step()
+            for jid in s.finished():
+                done[jid] = s.result(jid)
+    assert done[ids[1]].layers == want and done[ids[1]].status == 0
+    assert done[ids[0]].layers == oracle.growth(8, w.coxeter(8))[0]
+    assert done[ids[2]].layers == oracle.growth(7, w.pancake(7))[0]
 
 
 def _mahonian(n):
