@@ -217,7 +217,9 @@ int cg_growth_get_stats(cg_growth_t h, cg_growth_stats* out);
 /* Order of the group generated by the handle's generators (host Schreier-Sims). */
 uint64_t cg_growth_group_order(cg_growth_t h);
 
-/* Release the handle and every device buffer it owns.  NULL is accepted. */
+/* Release the handle and every device buffer it owns (the layers, visited set and scratch of
+ * the growth of Sections 2.1 and 3.1.2-3.1.3; buffers from a user allocator go back through its
+ * free callback).  NULL is accepted.  Returns CG_OK. */
 int cg_growth_destroy(cg_growth_t h);
 
 /* Human-readable name of a return code (static string). */
