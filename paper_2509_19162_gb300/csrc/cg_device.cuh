@@ -10,13 +10,21 @@
 
 namespace cg {
 
-__device__ __forceinline__ uint64_t rotl64(uint64_t x, unsigned r) {
-    return (x << r) | (x >> ((64u - r) & 63u));
+// Rotation of the 64-bit word hi:lo left by r (0..63), as two 32-bit funnel shifts: the halves
+// trade places when r >= 32, then each result half is the top word of a 64-bit concatenation
+// shifted left by r mod 32.  (A 64-bit rotate by a run-time amount costs several times this.)
+__device__ __forceinline__ void rotl_halves(uint32_t lo, uint32_t hi, unsigned r, uint32_t& rlo,
+                                            uint32_t& rhi) {
+    const bool swap = (r & 32u) != 0;
+    const uint32_t a = swap ? hi : lo, b = swap ? lo : hi;
+    rhi = __funnelshift_l(a, b, r);
+    rlo = __funnelshift_l(b, a, r);
 }
 
 // t[i] = s[g[i]] on packed keys (see GenSM): a range reversal by bit reversal, otherwise a union
-// of rotated, masked copies of s.  kRev = false compiles the shift-and-mask form only: for
-// kernels that run generators of at most 16 elements, where reversals are in that form.
+// of rotated, masked copies of s, built on 32-bit halves.  kRev = false compiles the
+// shift-and-mask form only: for kernels that run generators of at most 16 elements, where
+// reversals are in that form.
 template <bool kRev = true>
 __device__ __forceinline__ uint64_t apply_gen(const GenSM& g, uint64_t s) {
     if (kRev && g.kind == 1) {
@@ -27,11 +35,18 @@ __device__ __forceinline__ uint64_t apply_gen(const GenSM& g, uint64_t s) {
         r = sh >= 0 ? (r >> sh) : (r << -sh);
         return (s & ~g.mask[0]) | (r & g.mask[0]);
     }
-    uint64_t t = 0;
+    const uint32_t lo = (uint32_t)s, hi = (uint32_t)(s >> 32);
+    uint32_t tlo = 0, thi = 0;
     const uint32_t nt = g.nterms;
-#pragma unroll 4
-    for (uint32_t i = 0; i < nt; ++i) t |= rotl64(s, g.rot[i]) & g.mask[i];
-    return t;
+#pragma unroll 2
+    for (uint32_t i = 0; i < nt; ++i) {
+        uint32_t rlo, rhi;
+        rotl_halves(lo, hi, g.rot[i], rlo, rhi);
+        const uint64_t m = g.mask[i];
+        tlo |= rlo & (uint32_t)m;
+        thi |= rhi & (uint32_t)(m >> 32);
+    }
+    return ((uint64_t)thi << 32) | tlo;
 }
 
 // 64-bit finaliser of MurmurHash3 (A. Appleby, public domain): a bijection of uint64.

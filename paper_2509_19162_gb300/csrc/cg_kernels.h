@@ -21,9 +21,13 @@ cudaError_t launch_resume_units(JobDev* d_jobs, int njobs, unsigned long long* d
 // n > 0: the jobs' n, for the kernel variants compiled per n (a single rank-bitmap job).
 // d_adm (device): a batch launch that admits the jobs as the window allows (AdmitDev); ubeg then
 // holds max_active + 1 entries and launch_admit_first must run first (on a zeroed control block).
+// host_job: for a launch of one job, the host's copy of its descriptor (the static fields the
+// device copy holds at this launch); the single-job kernels take them as a parameter.  Without
+// it one job runs through the kernel for several jobs.
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              int grid, int max_rounds, uint64_t timeout_ns, int ilp,
-                             cudaStream_t st, int n = 0, const AdmitDev* d_adm = nullptr);
+                             cudaStream_t st, int n = 0, const AdmitDev* d_adm = nullptr,
+                             const JobDev* host_job = nullptr);
 cudaError_t launch_admit_first(JobDev* d_jobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                                const AdmitDev* d_adm, cudaStream_t st);
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,

@@ -345,13 +345,44 @@ __device__ void close_round_single(JobDev* jobs, unsigned long long* ubeg, Ctl* 
 // keys out coalesced.
 constexpr int kStage = 512;
 
-__device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, int lane) {
+// The static fields of one job as the work loops use them.  A single-job launch receives them
+// as a kernel parameter (read from the constant bank: no load, no register, nothing to reload
+// after the atomics of a round); launches of several jobs read them from the job's descriptor
+// when a warp moves to another job.
+struct JobConst {
+    uint64_t* keys;
+    unsigned long long keys_cap;
+    uint64_t* table;
+    uint64_t table_mask;
+    unsigned long long bitmap_words;
+    int k;
+    int n;
+    int tagged;
+    int mode;
+};
+
+__device__ __forceinline__ JobConst job_const(const JobDev* J) {
+    JobConst c;
+    c.keys = J->keys;
+    c.keys_cap = J->keys_cap;
+    c.table = J->table;
+    c.table_mask = J->table_mask;
+    c.bitmap_words = J->bitmap_words;
+    c.k = J->k;
+    c.n = J->n;
+    c.tagged = J->tagged;
+    c.mode = J->mode;
+    return c;
+}
+
+__device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, const JobConst& c,
+                                            int lane) {
     if (cnt == 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&J->tail, (unsigned long long)cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    uint64_t* keys = J->keys;
-    const unsigned long long cap = J->keys_cap;
+    uint64_t* keys = c.keys;
+    const unsigned long long cap = c.keys_cap;
     bool over = false;
     for (int i = lane; i < cnt; i += 32) {
         const unsigned long long pos = base + i;
@@ -367,7 +398,8 @@ __device__ __forceinline__ void stage_flush(uint64_t* buf, int& cnt, JobDev* J, 
 // whole block (warps take their offsets from a block-level prefix of their counts) instead of
 // one per warp, since same-address atomics serialise at one L2 slice.  Called by every thread
 // of the block.
-__device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDev* J, int lane) {
+__device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDev* J, const JobConst& c,
+                                                  int lane) {
     __shared__ unsigned s_cnt[kGrowBlock / 32];
     __shared__ unsigned long long s_base;
     const int w = threadIdx.x >> 5;
@@ -384,8 +416,8 @@ __device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDe
     }
     __syncthreads();
     const unsigned long long base = s_base + s_cnt[w];
-    uint64_t* keys = J->keys;
-    const unsigned long long cap = J->keys_cap;
+    uint64_t* keys = c.keys;
+    const unsigned long long cap = c.keys_cap;
     bool over = false;
     for (int i = lane; i < cnt; i += 32) {
         const unsigned long long pos = base + i;
@@ -405,18 +437,18 @@ __device__ __forceinline__ void stage_flush_block(uint64_t* buf, int& cnt, JobDe
 // a tagged state, each lane runs only the other k - 1 generators (the generator index depends on
 // the lane), so the parent edge costs neither a probe nor the expansion and index arithmetic.
 template <int kProbeILP, int kMode, int kN = 0>
-__device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned long long idx,
-                                        unsigned long long hi, uint64_t* buf, int& cnt, int lane,
-                                        bool& overflow_seen, uint64_t s) {
+__device__ __forceinline__ void do_unit(JobDev* J, const JobConst& c, const GenSM* gens,
+                                        unsigned long long idx, unsigned long long hi, uint64_t* buf,
+                                        int& cnt, int lane, bool& overflow_seen, uint64_t s) {
     const bool active = idx < hi;
-    const int n = J->n;
-    const bool tagged = J->tagged != 0;
+    const int n = c.n;
+    const bool tagged = c.tagged != 0;
     unsigned tag = 0;                       // 1 + generator that leads back to the parent
     if (tagged) {
         tag = (unsigned)(s >> 60);
         s &= kKeyBits60;
     }
-    const int k = J->k;
+    const int k = c.k;
     const bool skip = tagged && __all_sync(0xffffffffu, !active || tag != 0);
     const int iters = skip ? k - 1 : k;
     for (int j0 = 0; j0 < iters; j0 += kProbeILP) {
@@ -435,12 +467,12 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
             if (active && i < ng && tag != (unsigned)(gi[i] + 1)) vmask |= 1u << i;
         }
         if (kMode == kVisitBitmap)
-            bitmap_insert_multi<kProbeILP, kN>(reinterpret_cast<unsigned*>(J->table), J->bitmap_words,
+            bitmap_insert_multi<kProbeILP, kN>(reinterpret_cast<unsigned*>(c.table), c.bitmap_words,
                                                n, t, res, vmask);
         else if (kMode == 1)
-            table_insert_multi_sector<kProbeILP>(J->table, J->table_mask, t, res, vmask, kMaxProbe);
+            table_insert_multi_sector<kProbeILP>(c.table, c.table_mask, t, res, vmask, kMaxProbe);
         else
-            table_insert_multi_slot<kProbeILP>(J->table, J->table_mask, t, res, vmask, kMaxProbe);
+            table_insert_multi_slot<kProbeILP>(c.table, c.table_mask, t, res, vmask, kMaxProbe);
         bool bad = false;
 #pragma unroll
         for (int i = 0; i < kProbeILP; ++i) bad |= (res[i] < 0);
@@ -457,7 +489,7 @@ __device__ __forceinline__ void do_unit(JobDev* J, const GenSM* gens, unsigned l
             }
             cnt += __popc(fresh);
             __syncwarp();
-            if (cnt > kStage - 32) stage_flush(buf, cnt, J, lane);
+            if (cnt > kStage - 32) stage_flush(buf, cnt, J, c, lane);
         }
     }
 }
@@ -469,52 +501,35 @@ __device__ __forceinline__ unsigned long long draw_unit(unsigned long long& coun
     return __shfl_sync(0xffffffffu, u, 0);
 }
 
-// The work phase of a round of a single job, over units [b0, ue) drawn by this block's warps
-// from `s_unit` (set to b0 by the caller, followed by __syncthreads).  Ends with the block's
-// flush of newly found states.  The next unit's frontier key is loaded while the current unit
-// is processed.
+// The work phase of a round of a single job: the warp takes units w0, w0 + W, w0 + 2W, ... of
+// the frontier keys[lo, hi) (W = warps taking part, w0 = this warp's place among them), so the
+// units are dealt out with no atomics and the warp knows its next unit in advance: the next
+// unit's frontier key is loaded while the current one is processed.  Ends with the block's
+// flush of newly found states (every thread of the block calls this).  The job's overflow flag
+// (buffers full: the host grows them and redoes the layer) is read every 16 units, one unit
+// before its value is needed.
 template <int kProbeILP, int kMode, int kN = 0>
-__device__ __forceinline__ void phase_single(JobDev* J, const GenSM* gens, unsigned long long& s_unit,
-                                             unsigned long long ue, unsigned long long total,
-                                             unsigned long long* dyn, uint64_t* buf, int lane,
-                                             unsigned long long lo, unsigned long long hi) {
+__device__ __forceinline__ void phase_single(JobDev* J, const JobConst& c, const GenSM* gens,
+                                             unsigned long long w0, unsigned long long W, uint64_t* buf,
+                                             int lane, unsigned long long lo, unsigned long long hi) {
     int cnt = 0;
     bool overflow_seen = false;
-    unsigned iter = 0;
-    // The block's own range [.., ue) first; then units of the shared tail, two per draw from
-    // the global counter `dyn` (nullptr: no shared tail, e.g. when one block runs the round).
-    unsigned long long pending = ~0ull;
-    auto next_unit = [&]() -> unsigned long long {
-        const unsigned long long u = draw_unit(s_unit, lane);
-        if (u < ue) return u;
-        if (pending != ~0ull) {
-            const unsigned long long p = pending;
-            pending = ~0ull;
-            return p;
-        }
-        if (dyn == nullptr) return ~0ull;
-        unsigned long long d = 0;
-        if (lane == 0) d = atomicAdd(dyn, 2ull);
-        d = __shfl_sync(0xffffffffu, d, 0);
-        if (d >= total) return ~0ull;
-        if (d + 1 < total) pending = d + 1;
-        return d;
-    };
-    unsigned long long b = next_unit();
-    uint64_t s_next = (b != ~0ull && lo + (b << 5) + lane < hi) ? __ldcg(J->keys + lo + (b << 5) + lane) : 0;
-    while (b != ~0ull) {
+    const unsigned long long total = (hi - lo + 31) >> 5;
+    unsigned long long u = w0;
+    uint64_t s_next = (u < total && lo + (u << 5) + lane < hi) ? __ldcg(c.keys + lo + (u << 5) + lane) : 0;
+    int ov = 0;
+    for (unsigned iter = 0; u < total; ++iter) {
         const uint64_t s_cur = s_next;
-        const unsigned long long nb = next_unit();
-        s_next = (nb != ~0ull && lo + (nb << 5) + lane < hi) ? __ldcg(J->keys + lo + (nb << 5) + lane) : 0;
-        do_unit<kProbeILP, kMode, kN>(J, gens, lo + (b << 5) + lane, hi, buf, cnt, lane, overflow_seen, s_cur);
-        // Stop early once any warp found the job's buffers full (the layer will be redone after
-        // the host grows them).
-        if ((++iter & 3u) == 0 && __any_sync(0xffffffffu, ld_relaxed_int(&J->overflow)))
-            overflow_seen = true;
+        const unsigned long long nu = u + W;
+        s_next = (nu < total && lo + (nu << 5) + lane < hi) ? __ldcg(c.keys + lo + (nu << 5) + lane) : 0;
+        const bool check = (iter & 15u) == 15u;
+        if ((iter & 15u) == 14u) ov = ld_relaxed_int(&J->overflow);
+        do_unit<kProbeILP, kMode, kN>(J, c, gens, lo + (u << 5) + lane, hi, buf, cnt, lane, overflow_seen, s_cur);
+        if (check && __any_sync(0xffffffffu, ov)) overflow_seen = true;
         if (overflow_seen) break;
-        b = nb;
+        u = nu;
     }
-    stage_flush_block(buf, cnt, J, lane);
+    stage_flush_block(buf, cnt, J, c, lane);
 }
 
 // Barrier payload of a single-job round: the next frontier's size, with this bit set when the
@@ -528,11 +543,11 @@ constexpr unsigned long long kSoloUnits = kGrowBlock / 32;
 constexpr int kSmemGens = 32;
 
 // kMulti = false: the launch has exactly one job (the single-job path only is compiled, which
-// keeps registers low); true: any number of jobs.
+// keeps registers low), whose static fields are `jc`; true: any number of jobs (`jc` unused).
 template <int kProbeILP, int kMode, bool kMulti, int kN = 0>
 __global__ void __launch_bounds__(kGrowBlock, kMode == 2 ? 4 : ((kMode == 1 && kProbeILP >= 3) ? 2 : 3))
 hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, int max_rounds,
-                 uint64_t timeout_ns, const AdmitDev* adm) {
+                 uint64_t timeout_ns, const AdmitDev* adm, const JobConst jc) {
     __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
     __shared__ GenSM s_gens[kSmemGens];
     __shared__ unsigned long long s_unit;
@@ -573,17 +588,21 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         // their range early take from it); smaller rounds are split in equal ranges only.
         const bool shared_tail = total >= 16ull * gridDim.x;
         const unsigned long long stat = shared_tail ? static_units(total) : total;
-        if (threadIdx.x == 0) s_unit = stat * blockIdx.x / gridDim.x;   // this block's first unit
-        __syncthreads();
+        if (kMulti) {
+            if (threadIdx.x == 0) s_unit = stat * blockIdx.x / gridDim.x;   // this block's first unit
+            __syncthreads();
+        }
         int cnt = 0;
         bool overflow_seen = false;
         if (!kMulti) {
-            phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, stat * (blockIdx.x + 1) / gridDim.x,
-                                               total, shared_tail ? &ctl->dyn_next : nullptr, buf, lane,
-                                               lo, hi);
+            // unit u goes to block u mod grid, so that a small round spreads over every SM
+            const unsigned long long W = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+            const unsigned long long w0 = (unsigned long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+            phase_single<kProbeILP, kMode, kN>(jobs, jc, single_gens, w0, W, buf, lane, lo, hi);
         } else {
             int cur = -1;
             JobDev* J = nullptr;
+            JobConst c = {};
             unsigned long long lo = 0, hi = 0, u0 = 0;
             const unsigned long long ue = stat * (blockIdx.x + 1) / gridDim.x;
             unsigned long long pending = ~0ull;
@@ -612,9 +631,10 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
             for (unsigned long long u = next_unit(); u != ~0ull; u = next_unit()) {
                 const int slot = find_job(ubeg, nj, u);
                 if (slot != cur) {
-                    if (J) stage_flush(buf, cnt, J, lane);
+                    if (J) stage_flush(buf, cnt, J, c, lane);
                     cur = slot;
                     J = jobs + (act ? __ldcg(act + slot) : slot);
+                    c = job_const(J);
                     lo = ld_relaxed_ull(&J->lo);
                     hi = ld_relaxed_ull(&J->hi);
                     u0 = ld_relaxed_ull(ubeg + slot);
@@ -626,13 +646,13 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     const unsigned long long idx = first + lane;
                     const uint64_t s0 = idx < hi ? __ldcg(J->keys + idx) : 0;
                     // In the rank-bitmap variant a launch may mix jobs of both visited-set kinds.
-                    if (kMode == kVisitBitmap && J->mode != kVisitBitmap)
-                        do_unit<kProbeILP, kVisitHash>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                    if (kMode == kVisitBitmap && c.mode != kVisitBitmap)
+                        do_unit<kProbeILP, kVisitHash>(J, c, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
                     else
-                        do_unit<kProbeILP, kMode>(J, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                        do_unit<kProbeILP, kMode>(J, c, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
                 }
             }
-            if (J) stage_flush(buf, cnt, J, lane);
+            if (J) stage_flush(buf, cnt, J, c, lane);
         }
         // One barrier per round: the last block to finish the round closes it (layer counts,
         // stop tests, next round's work layout) and then releases the others.
@@ -651,10 +671,8 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     ++round;
                     solo = true;
                     const unsigned long long slo = s_lo, shi = s_hi;
-                    if (threadIdx.x == 0) s_unit = 0;
-                    __syncthreads();
-                    phase_single<kProbeILP, kMode, kN>(jobs, single_gens, s_unit, t, t, nullptr, buf, lane,
-                                                       slo, shi);
+                    phase_single<kProbeILP, kMode, kN>(jobs, jc, single_gens, threadIdx.x >> 5,
+                                                       blockDim.x >> 5, buf, lane, slo, shi);
                     __syncthreads();
                     close_round_single(jobs, ubeg, ctl, &s_fresh, &s_lo, &s_hi);
                 }
@@ -812,7 +830,7 @@ __global__ void finish_insert_count_kernel(unsigned long long* count, const int*
 int hash_grow_block() { return kGrowBlock; }
 
 namespace {
-using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t, const AdmitDev*);
+using GrowFn = void (*)(JobDev*, int, unsigned long long*, Ctl*, int, uint64_t, const AdmitDev*, const JobConst);
 // Kernel variants: `ilp` generators per thread (1..4); +8 selects whole-sector table probing,
 // +16 the rank bitmap; multi = launches of several jobs.
 template <bool M>
@@ -884,8 +902,23 @@ cudaError_t launch_admit_first(JobDev* d_jobs, unsigned long long* d_ubeg, Ctl* 
 
 cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ubeg, Ctl* d_ctl,
                              int grid, int max_rounds, uint64_t timeout_ns, int ilp, cudaStream_t st,
-                             int n, const AdmitDev* d_adm) {
+                             int n, const AdmitDev* d_adm, const JobDev* host_job) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    // The single-job kernels take the job's static fields as a parameter: without the host's
+    // copy of them, one job runs through the general kernel.
+    const bool multi = njobs > 1 || d_adm != nullptr || host_job == nullptr;
+    JobConst jc = {};
+    if (!multi) {
+        jc.keys = host_job->keys;
+        jc.keys_cap = host_job->keys_cap;
+        jc.table = host_job->table;
+        jc.table_mask = host_job->table_mask;
+        jc.bitmap_words = host_job->bitmap_words;
+        jc.k = host_job->k;
+        jc.n = host_job->n;
+        jc.tagged = host_job->tagged;
+        jc.mode = host_job->mode;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kGrowBlock);
@@ -896,8 +929,8 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, njobs > 1 || d_adm != nullptr, n), d_jobs, njobs, d_ubeg,
-                              d_ctl, max_rounds, timeout_ns, d_adm);
+    return cudaLaunchKernelEx(&cfg, grow_fn(ilp, multi, n), d_jobs, njobs, d_ubeg, d_ctl, max_rounds,
+                              timeout_ns, d_adm, jc);
 }
 
 cudaError_t launch_rebuild_table(const uint64_t* keys, unsigned long long count, uint64_t* table,

@@ -606,7 +606,7 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
     for (;;) {
         if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
         if ((e = cg::launch_hash_grow(h->d_job, 1, h->d_ubeg, h->d_ctl, grid, cg::kMaxLayers + 1,
-                                      kTimeoutNs, ilp, st, h->n)) != cudaSuccess)
+                                      kTimeoutNs, ilp, st, h->n, nullptr, &J)) != cudaSuccess)
             return cuda_rc(e);
         if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
         h->stats.launches += 1;

@@ -243,7 +243,7 @@ extern "C" int cg_growth_run_noalloc(int n, int k, const uint8_t* gens, int inve
     if ((e = cudaMemsetAsync(d_ctl, 0, sizeof(cg::Ctl), st))) return cuda_rc(e);
     if ((e = cg::launch_init_jobs(d_job, 1, d_ubeg, d_ctl, st))) return cuda_rc(e);
     if ((e = cg::launch_hash_grow(d_job, 1, d_ubeg, d_ctl, grid, cg::kMaxLayers + 1, kTimeoutNs,
-                                  ilp, st)))
+                                  ilp, st, 0, nullptr, &J)))
         return cuda_rc(e);
     cg::Ctl ctl;
     if ((e = cudaMemcpyAsync(&J, d_job, sizeof(J), cudaMemcpyDeviceToHost, st))) return cuda_rc(e);
