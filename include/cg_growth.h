@@ -57,10 +57,10 @@ extern "C" {
                                   most half of mem_cap and 16 GiB (else CG_EINVAL at run).
                                   AUTO picks it when it fits and the group fills at least 1/512
                                   of S_n, else HASH                                           */
-#define CG_STRATEGY_SWEEP   4  /* bitmask BFS (Section 3.1.3): the visited set and the last
-                                  three layers are bitmaps over the n! Lehmer ranks (4 bits per
+#define CG_STRATEGY_SWEEP   4  /* bitmask BFS (Section 3.1.3): the visited set and two
+                                  layers are bitmaps over the n! Lehmer ranks (3 bits per
                                   element of S_n, nothing per state), so the whole of S_14 fits
-                                  in 44 GB; any generating set; start with distinct values;
+                                  in 33.4 GB; any generating set; start with distinct values;
                                   needs n <= 14 and the bitmaps within mem_cap (else CG_EINVAL
                                   at run)                                                      */
 

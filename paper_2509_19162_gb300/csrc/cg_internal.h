@@ -144,17 +144,18 @@ static_assert(offsetof(JobDev, tail) % 16 == 0 && offsetof(JobDev, radius) == of
                   offsetof(JobDev, status) == offsetof(JobDev, radius) + 4,
               "JobDev: tail, radius, status must form one aligned 16-byte vector");
 
-// One growth of the sweep strategy: the visited set and the last three layers are bitmaps over
-// the position-major Lehmer ranks 0..n!-1 (one bit per element of S_n).  Layer r lives in
-// F[r % 3]; its nonempty 1024-rank blocks (32 words of F) are listed, once each, in
-// L[r % 3][0, lcount[r % 3]); S[r % 3] has one bit per block and is what makes a block's entry
-// in the list unique.
+// One growth of the sweep strategy: the visited set and two layers are bitmaps over the
+// position-major Lehmer ranks 0..n!-1 (one bit per element of S_n each: 3 bits per element, as in
+// the bitmask BFS of Section 3.1.3).  Layer r lives in F[r & 1]; its nonempty 1024-rank blocks
+// (32 words of F) are listed, once each, in L[r & 1][0, lcount[r & 1]); S[r & 1] has one bit per
+// block and is what makes a block's entry in the list unique.  Round r first clears layer r - 1
+// (the other bitmap, its listed blocks) and then writes layer r + 1 there.
 struct alignas(128) SweepDev {
     // static, written by the host
     unsigned* V;               // visited
-    unsigned* F[3];            // layers r-1, r, r+1 in rotation
-    unsigned* S[3];            // per-block bits of F (one bit per 32 words)
-    unsigned* L[3];            // nonempty blocks of F (block index = rank >> 10)
+    unsigned* F[2];            // layer r in F[r & 1]; the other holds layer r-1, then r+1
+    unsigned* S[2];            // per-block bits of F (one bit per 32 words)
+    unsigned* L[2];            // nonempty blocks of F (block index = rank >> 10)
     const GenSM* gens;         // k entries
     uint64_t* layer_sizes;     // layers_cap entries; [0] = 1
     uint64_t nblocks;          // 1024-rank blocks: every F has 32 * nblocks words
@@ -167,7 +168,7 @@ struct alignas(128) SweepDev {
     // dynamic, updated during a run
     alignas(128) unsigned long long grab;   // next work item of the round
     unsigned long long fresh;               // states found in the round
-    unsigned long long lcount[3];           // entries of L[i]
+    unsigned long long lcount[2];           // entries of L[i]
     int radius;                // radius of the frontier layer
     int status;                // JobStatus
 };

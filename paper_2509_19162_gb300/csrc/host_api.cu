@@ -270,13 +270,13 @@ uint64_t factorial(int n) {
     return f;
 }
 
-// Sweep strategy layout over S_n: 1024-rank blocks, and the bytes of V, three layer bitmaps,
+// Sweep strategy layout over S_n: 1024-rank blocks, and the bytes of V, two layer bitmaps,
 // their block bits and block lists.
 uint64_t sweep_blocks(int n) { return (factorial(n) + 1023) / 1024; }
 uint64_t sweep_bytes(int n) {
     const uint64_t nb = sweep_blocks(n);
     const uint64_t words = nb * 32, sum = (nb + 31) / 32;
-    return 4 * (4 * words + 3 * sum + 3 * nb) + 4096;
+    return 4 * (3 * words + 2 * sum + 2 * nb) + 4096;
 }
 
 // 32-bit words of a rank bitmap over S_n, rounded up to whole 8-byte slots.
@@ -423,7 +423,7 @@ struct cg_growth {
     uint64_t wtable_slots = 0;
     cg::WideDev host_wide{};
 
-    // sweep strategy: visited bitmap, three layer bitmaps with block bits and block lists
+    // sweep strategy: visited bitmap, two layer bitmaps with block bits and block lists
     SweepDev* d_sweep = nullptr;
     unsigned* d_sw = nullptr;                    // one allocation holding all of the below
     uint64_t sw_bytes = 0;
@@ -797,7 +797,7 @@ int run_wide(cg_growth* h, cudaStream_t st, int* final_status) {
 }
 
 // ---- sweep strategy driver -----------------------------------------------------------------
-// Bitmaps over S_n for the visited set and the last three layers (sweep_path.cu); one
+// Bitmaps over S_n for the visited set and two layers (sweep_path.cu: 3 bits per element); one
 // persistent launch runs every layer step.  Needs a start with distinct values and n <= 14.
 
 // AUTO takes the sweep for the whole growth (no radius or layer-size limit) of a dense subgroup
@@ -828,14 +828,14 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
         if (!h->d_sw || !h->d_sweep) return CG_ENOMEM;
         h->sw_bytes = bytes;
     }
-    // layout: V | F0 F1 F2 | S0 S1 S2 | L0 L1 L2   (32-bit words)
+    // layout: V | F0 F1 | S0 S1 | L0 L1   (32-bit words)
     SweepDev D;
     std::memset(&D, 0, sizeof(D));
     unsigned* p = h->d_sw;
     D.V = p; p += words;
-    for (int i = 0; i < 3; ++i) { D.F[i] = p; p += words; }
-    for (int i = 0; i < 3; ++i) { D.S[i] = p; p += nsum; }
-    for (int i = 0; i < 3; ++i) { D.L[i] = p; p += nb; }
+    for (int i = 0; i < 2; ++i) { D.F[i] = p; p += words; }
+    for (int i = 0; i < 2; ++i) { D.S[i] = p; p += nsum; }
+    for (int i = 0; i < 2; ++i) { D.L[i] = p; p += nb; }
     D.gens = h->d_gens;
     D.layer_sizes = h->d_layers;
     D.nblocks = nb;
@@ -860,7 +860,7 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
         D.start_rank = r;
     }
     // V, F and S start empty (the lists need no clearing: lcount bounds them)
-    cudaError_t e = cudaMemsetAsync(D.V, 0, (4 * words + 3 * nsum) * 4, st);
+    cudaError_t e = cudaMemsetAsync(D.V, 0, (3 * words + 2 * nsum) * 4, st);
     if (e != cudaSuccess) return cuda_rc(e);
     if ((e = cudaMemcpyAsync(h->d_sweep, &D, sizeof(D), cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_rc(e);
@@ -1423,7 +1423,7 @@ int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64
         return cuda_rc(e);
     }
     if (h->last_is_sweep) {
-        // unrank the last layer's bitmap (layer R lives in F[R % 3], its blocks in L[R % 3])
+        // unrank the last layer's bitmap (layer R lives in F[R & 1], its blocks in L[R & 1])
         const SweepDev& D = h->host_sweep;
         uint64_t cnt = 0;
         cudaError_t e = cudaMemcpy(&cnt, h->d_layers + D.radius, 8, cudaMemcpyDeviceToHost);
@@ -1434,7 +1434,7 @@ int cg_growth_last_layer(cg_growth_t h, uint64_t* keys_out, uint64_t cap, uint64
         uint64_t* d_out = (uint64_t*)dev_alloc(cnt * 8 + 64, nullptr);
         if (!d_out) return CG_ENOMEM;
         unsigned long long* d_count = (unsigned long long*)(d_out + cnt);
-        const int w = D.radius % 3;
+        const int w = D.radius & 1;
         int grid = 0;
         cudaDeviceGetAttribute(&grid, cudaDevAttrMultiProcessorCount, h->device);
         e = cudaMemsetAsync(d_count, 0, 8, nullptr);

@@ -1,7 +1,8 @@
 // Sweep strategy of the growth library: breadth-first growth with the visited set and the
 // layers held as bitmaps over S_n, the paper's bitmask BFS (Section 3.1.3: a few bits per
-// element of the group instead of a list of states).  Nothing per state is stored but bits, so a
-// growth needs 4 n!/8 bytes whatever its layers hold: 43.6 GB for all of S_14.
+// element of the group instead of a list of states).  Nothing per state is stored but bits --
+// the visited set and two layers, 3 bits per element of S_n -- so a growth needs 3 n!/8 bytes
+// (plus about 1 % for block lists) whatever its layers hold: 33.4 GB for all of S_14.
 //
 // Index of a permutation: the position-major Lehmer rank
 //     rank(s) = sum_{i=1}^{n-1} d_i * i!,   d_i = #{ j < i : s_j < s_i },
@@ -11,8 +12,8 @@
 // the block being expanded, which the L2 serves.
 //
 // One round (layer step) of the persistent cooperative kernel:
-//   the blocks of layer r-1 are cleared (F and S), so that its buffers are empty when they
-//   receive layer r+2;
+//   the listed blocks of layer r-1 are cleared (F and S), and after a grid barrier its buffers,
+//   empty, receive layer r+1;
 //   the nonempty 1024-rank blocks of layer r are expanded: their states are unranked, every
 //   generator applied, the images ranked and test-and-set in V (one atomicOr each); a new state
 //   sets its bit in F_{r+1}, the first bit of a block enters the block in L_{r+1} (per-warp
@@ -169,8 +170,6 @@ __device__ void sweep_close(SweepDev& D, Ctl* ctl) {
         else if (D.stop_above > 0 && fresh > D.stop_above) W.status = kTruncAbove;
         else if (r1 + 1 >= D.layers_cap) W.status = kTruncRadius;
     }
-    // The list of layer r-1 was cleared in this round: it receives layer r+2.
-    W.lcount[(r + 2) % 3] = 0;
     W.fresh = 0;
     W.grab = 0;
     *(volatile int*)&ctl->rounds += 1;
@@ -203,17 +202,31 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
     for (int round = 0; round < max_rounds; ++round) {
         if (ld_relaxed_int(&D.status) != kRunning) break;
         const int r = ld_relaxed_int(&D.radius);
-        const int cur = r % 3, nxt = (r + 1) % 3, prv = (r + 2) % 3;
+        // Layer r is F[r & 1]; layer r + 1 goes to the other bitmap, which still holds layer
+        // r - 1 (3 bits per element of S_n: V and two layers).  That layer is cleared first --
+        // its listed blocks, one per thread -- and after a grid barrier the round expands layer r.
+        const int cur = r & 1, nxt = cur ^ 1;
         unsigned* F = D.F[cur];
         unsigned* N = D.F[nxt];
         unsigned* SN = D.S[nxt];
-        unsigned* P = D.F[prv];
-        unsigned* SP = D.S[prv];
         const unsigned* Lc = D.L[cur];
-        const unsigned* Lp = D.L[prv];
         unsigned* Ln = D.L[nxt];
         unsigned long long* ln_count = &D.lcount[nxt];
-        const unsigned long long nprv = r > 0 ? ld_relaxed_ull(&D.lcount[prv]) : 0ull;
+        // (r > 0 decides the clearing phase for every block alike: the other list's count is
+        // read before the barrier, and blocks append to it only after it)
+        if (r > 0) {
+            const unsigned long long nprv = ld_relaxed_ull(&D.lcount[nxt]);
+            const unsigned long long nth = (unsigned long long)gridDim.x * kSweepBlock;
+            for (unsigned long long e = blockIdx.x * (unsigned long long)kSweepBlock + threadIdx.x; e < nprv; e += nth)
+                clear_block(N, SN, __ldcg(Ln + e));
+            unsigned long long word = 0;
+            const int arrive = grid_arrive(ctl, timeout_ns, word, nbar++);
+            if (arrive < 0) return;
+            if (arrive == 1) {
+                if (threadIdx.x == 0) *(volatile unsigned long long*)ln_count = 0;   // receives layer r + 1
+                grid_release(ctl, word, 0);
+            }
+        }
         if (threadIdx.x == 0) s_fresh = 0;
         __syncthreads();
 
@@ -222,8 +235,7 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
         // expands them 32 at a time, carrying fewer than 32 over to the next fetch, so every
         // chunk but the warp's last fills all lanes.  The blocks come in one of two orders:
         //   rank order (layers whose nonempty blocks fill at least 1/kRankFill of S_n): units
-        //       are drawn one at a time from one counter; the first ceil(|L_{r-1}|/32) clear 32
-        //       blocks of layer r-1 each (F and S, one per lane); the rest cover S_n in rank
+        //       are drawn one at a time from one counter and cover S_n in rank
         //       order, 2^lc blocks each, lc chosen so that a unit holds about kUnitStates
         //       states when they are spread evenly, and the warp finds their nonempty blocks
         //       from the block bits of layer r.  The warps of the grid then work within a
@@ -231,9 +243,8 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
         //       short-support generators fall, so those visited-set accesses hit L2;
         //   discovery order (sparser layers, which may crowd into few ranges of S_n, and every
         //       layer when the visited bitmap fits L2 anyway): units
-        //       are the 32 |L_r| words of the listed blocks of layer r, then the |L_{r-1}|
-        //       blocks of layer r-1 to clear, drawn in chunks of a quarter of the remaining
-        //       units' share of one warp (at least 32).
+        //       are the 32 |L_r| words of the listed blocks of layer r, drawn in chunks of a
+        //       quarter of the remaining units' share of one warp (at least 32).
         const unsigned long long ncur = ld_relaxed_ull(&D.lcount[cur]);
         const bool by_rank =
             order == kSweepOrderRank || (order == kSweepOrderAuto && ncur * kRankFill >= D.nblocks);
@@ -242,10 +253,8 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
         const unsigned long long want = fsize ? (kUnitStates * D.nblocks) / fsize : 1024ull;
         int lc = 0;
         while (lc < 10 && (1ull << lc) < want) ++lc;
-        const unsigned long long ncl = (nprv + 31) >> 5;
         const unsigned long long xunits = ncur * 32;
-        const unsigned long long units =
-            by_rank ? ncl + ((D.nblocks + (1ull << lc) - 1) >> lc) : xunits + nprv;
+        const unsigned long long units = by_rank ? (D.nblocks + (1ull << lc) - 1) >> lc : xunits;
         const unsigned* S = D.S[cur];
         unsigned fresh = 0;
         int lcnt = 0;
@@ -302,14 +311,9 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
                         exhausted = true;
                         continue;
                     }
-                    if (u < ncl) {
-                        const unsigned long long e = (u << 5) + lane;
-                        if (e < nprv) clear_block(P, SP, __ldcg(Lp + e));
-                        continue;
-                    }
                     // blocks [b0, b1) of S_n: lane l holds the bits of blocks 32 (wb + l) ..
                     // 32 (wb + l) + 31 that fall in the range (at most 32 words: 2^lc <= 1024)
-                    const unsigned long long b0 = (u - ncl) << lc;
+                    const unsigned long long b0 = u << lc;
                     const unsigned long long b1 =
                         b0 + (1ull << lc) < D.nblocks ? b0 + (1ull << lc) : D.nblocks;
                     wb = b0 >> 5;
@@ -351,14 +355,10 @@ sweep_grow_kernel(SweepDev* Dp, Ctl* ctl, int max_rounds, uint64_t timeout_ns, i
                 }
                 const unsigned long long u = ua + lane;
                 if (u < ub) {
-                    if (u < xunits) {
-                        const unsigned blk = __ldcg(Lc + (u >> 5));
-                        const unsigned w = (unsigned)(u & 31u);
-                        fw = __ldcg(F + (uint64_t)blk * 32 + w);
-                        lbase = ((uint64_t)blk << 10) | (w << 5);
-                    } else {
-                        clear_block(P, SP, __ldcg(Lp + (u - xunits)));
-                    }
+                    const unsigned blk = __ldcg(Lc + (u >> 5));
+                    const unsigned w = (unsigned)(u & 31u);
+                    fw = __ldcg(F + (uint64_t)blk * 32 + w);
+                    lbase = ((uint64_t)blk << 10) | (w << 5);
                 }
                 ua = ua + 32 < ub ? ua + 32 : ub;
             }
@@ -424,7 +424,6 @@ __global__ void sweep_init_kernel(SweepDev* Dp) {
     D.L[0][0] = blk;
     D.lcount[0] = 1;
     D.lcount[1] = 0;
-    D.lcount[2] = 0;
     D.layer_sizes[0] = 1;
     D.grab = 0;
     D.fresh = 0;
