@@ -913,6 +913,12 @@ int run_sweep(cg_growth* h, cudaStream_t st, int* final_status) {
 // Bytes of the candidate buffer and sort scratch for q candidates.
 uint64_t cand_bytes(uint64_t q) { return q * 8 + cg::sort_scratch_bytes(q); }
 
+// First key bit the radix passes need: the states of a growth from a permutation are
+// permutations, whose element at position 0 is the one value missing from the others, so two
+// keys that agree above it are equal and ordering them on bits [w, w n) gives the order of the
+// whole keys (one 8-bit pass fewer for n = 11).  Other vectors sort on all their bits.
+int sort_low_bit(const cg_growth* h) { return h->start_is_perm && h->width == 4 ? 4 : 0; }
+
 // Candidate buffer and scratch for q candidates (kept when larger, unless shrink).
 int ensure_cand(cg_growth* h, uint64_t q, cudaStream_t st, bool shrink = false) {
     if (h->d_cand && (q == h->cand_cap || (q < h->cand_cap && !shrink))) return CG_OK;
@@ -955,8 +961,9 @@ int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, 
                int radius, int* final_status) {
     const uint64_t mem = h->mem_cap ? h->mem_cap : kDefaultMemCap;
     const int bits = h->width * h->n;
-    const int P = cg::sort_passes(bits);
-    const int top_shift = 8 * (P - 1);
+    const int lo = sort_low_bit(h);
+    const int P = cg::sort_passes(bits, lo);
+    const int top_shift = lo + 8 * (P - 1);
     int nxt = 3 - cur - prev;
     cudaError_t e = cudaSuccess;
     int rc = CG_OK;
@@ -996,7 +1003,7 @@ int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, 
         if (C <= h->cand_cap) {
             ranges.push_back({0u, 256u});
         } else {
-            if ((e = cg::launch_candidate_hist(src, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cg::launch_candidate_hist(src, bits, sc, st, lo)) != cudaSuccess) return cuda_rc(e);
             std::vector<unsigned long long> th(256);
             if ((e = cudaMemcpyAsync(th.data(), sc.ghist + (size_t)(P - 1) * 256, 256 * 8, cudaMemcpyDeviceToHost,
                                      st)) != cudaSuccess)
@@ -1021,7 +1028,7 @@ int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, 
             if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
             uint64_t Cc = C;
             if (ranges.size() == 1) {
-                if ((e = cg::launch_expand_sort(src, h->d_cand, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+                if ((e = cg::launch_expand_sort(src, h->d_cand, bits, sc, st, lo)) != cudaSuccess) return cuda_rc(e);
                 h->stats.launches += 1 + P;
             } else {
                 if ((e = cg::launch_expand_filter(src, top_shift, rg.first, rg.second, h->d_cand, h->cand_cap,
@@ -1032,7 +1039,7 @@ int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, 
                     return cuda_rc(e);
                 if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
                 Cc = std::min<uint64_t>(got, h->cand_cap);
-                if ((e = cg::launch_radix_sort(h->d_cand, Cc, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
+                if ((e = cg::launch_radix_sort(h->d_cand, Cc, bits, sc, st, lo)) != cudaSuccess) return cuda_rc(e);
                 h->stats.launches += 2 + P;
             }
             if ((e = cg::launch_unique_difference(h->d_cand, Cc, bs, nbs, 2, sc.keys_tmp, h->d_count, sc, st)) !=
@@ -1164,9 +1171,10 @@ int continue_sorted(cg_growth* h, cudaStream_t st, int* final_status) {
     const cg::SortScratch sc = cg::carve_sort_scratch(h->d_sort_scratch, h->cand_cap);
     const int bits = h->width * h->n;
     if ((e = cudaMemsetAsync(sc.err, 0, 4, st)) != cudaSuccess) return cuda_rc(e);
-    if ((e = cg::launch_radix_sort(h->d_L[prev], Fprev, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
-    if ((e = cg::launch_radix_sort(h->d_L[cur], Fcur, bits, sc, st)) != cudaSuccess) return cuda_rc(e);
-    h->stats.launches += 2 * (1 + cg::sort_passes(bits));
+    const int lo = sort_low_bit(h);
+    if ((e = cg::launch_radix_sort(h->d_L[prev], Fprev, bits, sc, st, lo)) != cudaSuccess) return cuda_rc(e);
+    if ((e = cg::launch_radix_sort(h->d_L[cur], Fcur, bits, sc, st, lo)) != cudaSuccess) return cuda_rc(e);
+    h->stats.launches += 2 * (1 + cg::sort_passes(bits, lo));
     h->sort_layers.assign(sizes.begin(), sizes.end());
     h->stats.switched_to_sort = 1;
     h->stats.sort_from = r;

@@ -39,22 +39,26 @@ struct ExpandSrc {
 
 cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, unsigned long long F,
                               uint64_t* out, cudaStream_t st);
-// Sort keys[0, n) ascending on their low `bits` bits (higher bits zero), in place.
+// Sort keys[0, n) ascending on their bits [lo, bits) (higher bits zero; lo > 0 only when the
+// bits below lo are decided by the others, as the element at position 0 of a permutation is),
+// in place.
 cudaError_t launch_radix_sort(uint64_t* keys, unsigned long long n, int bits, const SortScratch& s,
-                              cudaStream_t st);
+                              cudaStream_t st, int lo = 0);
 // Generate the k F candidates of src and write them sorted to out (k F keys, not s.keys_tmp).
 cudaError_t launch_expand_sort(const ExpandSrc& src, uint64_t* out, int bits, const SortScratch& s,
-                               cudaStream_t st);
+                               cudaStream_t st, int lo = 0);
 // out = the keys of sorted a that are first of their run and absent from every sorted b_j (at
 // most 2 sets), in order; *d_count = their number.
 cudaError_t launch_unique_difference(const uint64_t* a, unsigned long long na, const uint64_t* const* bs,
                                      const unsigned long long* nbs, int nb_sets, uint64_t* out,
                                      unsigned long long* d_count, const SortScratch& s, cudaStream_t st);
 
-// 8-bit LSD passes over `bits` key bits.
-int sort_passes(int bits);
-// Digit histograms (s.ghist[p * 256 + d], every pass p) of the candidates of src.
-cudaError_t launch_candidate_hist(const ExpandSrc& src, int bits, const SortScratch& s, cudaStream_t st);
+// 8-bit LSD passes over key bits [lo, bits).
+int sort_passes(int bits, int lo = 0);
+// Digit histograms (s.ghist[p * 256 + d], every pass p, digit p at bit lo + 8 p) of the
+// candidates of src.
+cudaError_t launch_candidate_hist(const ExpandSrc& src, int bits, const SortScratch& s, cudaStream_t st,
+                                  int lo = 0);
 // The candidates of src whose digit at `shift` lies in [d0, d1), appended to out (cap keys) in no
 // particular order; *d_count receives their number (d_err set if out is too small).
 cudaError_t launch_expand_filter(const ExpandSrc& src, int shift, unsigned d0, unsigned d1, uint64_t* out,

@@ -151,7 +151,7 @@ __global__ void expand_all_kernel(const GenSM* __restrict__ gens, int k, const u
 // ---- digit histograms of every pass in one read ------------------------------------------
 template <bool kGen>
 __global__ void __launch_bounds__(kBlock)
-hist_all_kernel(const uint64_t* __restrict__ keys, ExpandSrc src, unsigned long long n, int passes,
+hist_all_kernel(const uint64_t* __restrict__ keys, ExpandSrc src, unsigned long long n, int passes, int lo,
                 unsigned long long* __restrict__ ghist) {
     __shared__ unsigned s_h[kSortMaxPasses][kDigits];
     for (int i = threadIdx.x; i < kSortMaxPasses * kDigits; i += kBlock) (&s_h[0][0])[i] = 0;
@@ -159,7 +159,7 @@ hist_all_kernel(const uint64_t* __restrict__ keys, ExpandSrc src, unsigned long 
     const unsigned long long stride = (unsigned long long)gridDim.x * kBlock;
     for (unsigned long long i = blockIdx.x * (unsigned long long)kBlock + threadIdx.x; i < n; i += stride) {
         const uint64_t key = kGen ? gen_candidate(src, i) : keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(key >> (kRadixBits * p)) & (kDigits - 1)], 1u);
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(key >> (lo + kRadixBits * p)) & (kDigits - 1)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kDigits; i += kBlock) {
@@ -257,45 +257,130 @@ __device__ __forceinline__ unsigned long long gallop(const uint64_t* __restrict_
     return hi;
 }
 
+// First index j of sorted b[0, nb) with b[j] >= key (nb if none), found by one warp: each step
+// probes 32 evenly spaced positions of the remaining interval at once (one round trip) and keeps
+// the part between the last probe below key and the first one at or above it.
+__device__ unsigned long long warp_lower_bound(const uint64_t* __restrict__ b, unsigned long long nb, uint64_t key,
+                                               int lane) {
+    unsigned long long lo = 0, hi = nb;         // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const unsigned long long span = hi - lo;
+        const unsigned long long p = lo + span * (unsigned long long)(lane + 1) / 33;   // in [lo, hi)
+        const int c = __popc(__ballot_sync(0xffffffffu, b[p] < key));                  // lanes 0..c-1
+        const unsigned long long nlo = c ? lo + span * (unsigned long long)c / 33 + 1 : lo;
+        const unsigned long long nhi = c < 32 ? lo + span * (unsigned long long)(c + 1) / 33 : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const unsigned long long p = lo + (unsigned)lane;
+    return lo + __popc(__ballot_sync(0xffffffffu, p < hi && b[p] < key));
+}
+
+// Lower bound of key in the shared-memory slice s[j, ns), galloping from j.
+__device__ __forceinline__ unsigned gallop_smem(const uint64_t* s, unsigned ns, unsigned j, uint64_t key) {
+    if (j >= ns || s[j] >= key) return j;
+    unsigned lo = j, step = 1;
+    while (lo + step < ns && s[lo + step] < key) {
+        lo += step;
+        step <<= 1;
+    }
+    unsigned hi = lo + step < ns ? lo + step : ns;
+    while (hi - lo > 1) {
+        const unsigned mid = lo + ((hi - lo) >> 1);
+        if (s[mid] < key) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+// The keys of b0 and b1 that can match a tile's keys (those within the tile's first and last
+// key) are staged in shared memory when there are at most kSlice of them; each thread then walks
+// the staged slices instead of L2.  A slice larger than that falls back to the global walk.
+constexpr int kSlice = 2048;
+
 __global__ void __launch_bounds__(kBlock)
 unique_diff_kernel(const uint64_t* __restrict__ a, unsigned long long na, const uint64_t* __restrict__ b0,
                    unsigned long long nb0, const uint64_t* __restrict__ b1, unsigned long long nb1,
                    int first_of_run, uint64_t* __restrict__ out, unsigned long long* d_count,
                    unsigned long long* desc, unsigned* ticket, int ntiles, unsigned epoch, int* err) {
-    __shared__ uint64_t s_stage[kTile];
+    // the staged slices are done with before the survivors are staged for the output
+    __shared__ union {
+        uint64_t stage[kTile];
+        uint64_t slice[2][kSlice];
+    } s_m;
     __shared__ int s_tile;
     __shared__ unsigned long long s_prefix;
-    const int tid = threadIdx.x;
+    __shared__ unsigned long long s_j[2][2], s_lo[2], s_n[2];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) s_tile = (int)atomicAdd(ticket, 1u);
     __syncthreads();
     const int tile = s_tile;
-    const unsigned long long p0 = (unsigned long long)tile * kTile + (unsigned long long)tid * kItems;
+    const unsigned long long t0 = (unsigned long long)tile * kTile;
+    const unsigned long long t1 = t0 + kTile < na ? t0 + kTile : na;
+    // warps 0-3, in parallel: the slice of b0 (warps 0, 1) and b1 (warps 2, 3) holding the keys
+    // in [a[t0], a[t1 - 1]]: its first index (lower bound of a[t0]) and its end (lower bound of
+    // a[t1 - 1] + 1)
+    if (wid < 4) {
+        const int q = wid >> 1, end = wid & 1;
+        const uint64_t* b = q ? b1 : b0;
+        const unsigned long long nb = q ? nb1 : nb0;
+        const uint64_t key = end ? a[t1 - 1] : a[t0];
+        const unsigned long long j = (end && key == ~0ull) ? nb : warp_lower_bound(b, nb, key + (end ? 1 : 0), lane);
+        if (lane == 0) s_j[q][end] = j;
+    }
+    __syncthreads();
+    if (tid < 2) {
+        s_lo[tid] = s_j[tid][0];
+        s_n[tid] = s_j[tid][1] - s_j[tid][0];
+    }
+    __syncthreads();
+    bool staged[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        staged[q] = s_n[q] <= (unsigned long long)kSlice;
+        if (staged[q]) {
+            const uint64_t* b = q ? b1 : b0;
+            for (unsigned i = tid; i < (unsigned)s_n[q]; i += kBlock) s_m.slice[q][i] = b[s_lo[q] + i];
+        }
+    }
+    __syncthreads();
+    const unsigned long long p0 = t0 + (unsigned long long)tid * kItems;
     uint64_t key[kItems];
     unsigned keep = 0, cnt = 0;
 #pragma unroll
     for (int i = 0; i < kItems; ++i) key[i] = p0 + i < na ? a[p0 + i] : 0;
     uint64_t prev = (p0 > 0 && p0 - 1 < na) ? a[p0 - 1] : 0;
     bool has_prev = p0 > 0;
-    unsigned long long j0 = 0, j1 = 0;
+    unsigned long long j0 = 0, j1 = 0;         // global walks (slices too large)
+    unsigned k0 = 0, k1 = 0;                   // walks in the staged slices
     if (p0 < na) {
-        j0 = gallop(b0, nb0, 0, key[0]);          // galloping from 0 is a binary search
-        j1 = gallop(b1, nb1, 0, key[0]);
+        if (!staged[0]) j0 = gallop(b0, nb0, s_lo[0], key[0]);
+        if (!staged[1]) j1 = gallop(b1, nb1, s_lo[1], key[0]);
     }
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         if (p0 + i >= na) break;
         bool k = !(first_of_run && has_prev && prev == key[i]);
-        j0 = gallop(b0, nb0, j0, key[i]);
-        if (j0 < nb0 && b0[j0] == key[i]) k = false;
-        j1 = gallop(b1, nb1, j1, key[i]);
-        if (j1 < nb1 && b1[j1] == key[i]) k = false;
+        if (staged[0]) {
+            k0 = gallop_smem(s_m.slice[0], (unsigned)s_n[0], k0, key[i]);
+            if (k0 < (unsigned)s_n[0] && s_m.slice[0][k0] == key[i]) k = false;
+        } else {
+            j0 = gallop(b0, nb0, j0, key[i]);
+            if (j0 < nb0 && b0[j0] == key[i]) k = false;
+        }
+        if (staged[1]) {
+            k1 = gallop_smem(s_m.slice[1], (unsigned)s_n[1], k1, key[i]);
+            if (k1 < (unsigned)s_n[1] && s_m.slice[1][k1] == key[i]) k = false;
+        } else {
+            j1 = gallop(b1, nb1, j1, key[i]);
+            if (j1 < nb1 && b1[j1] == key[i]) k = false;
+        }
         keep |= (unsigned)k << i;
         cnt += k;
         prev = key[i];
         has_prev = true;
     }
     unsigned total = 0;
-    const unsigned excl = block_excl_scan<unsigned>(cnt, &total);
+    const unsigned excl = block_excl_scan<unsigned>(cnt, &total);   // ends with __syncthreads
     if (tid == 0) {
         s_prefix = look_back(desc, 1, tile, total, epoch, err);
         if (tile == ntiles - 1 && *(volatile int*)err == 0) *d_count = s_prefix + total;
@@ -303,11 +388,11 @@ unique_diff_kernel(const uint64_t* __restrict__ a, unsigned long long na, const 
     unsigned pos = excl;
 #pragma unroll
     for (int i = 0; i < kItems; ++i)
-        if (keep >> i & 1u) s_stage[pos++] = key[i];
+        if (keep >> i & 1u) s_m.stage[pos++] = key[i];
     __syncthreads();
     const unsigned long long o = s_prefix;
     for (unsigned i = tid; i < total; i += kBlock)
-        if (o + i < na) out[o + i] = s_stage[i];
+        if (o + i < na) out[o + i] = s_m.stage[i];
 }
 
 // ---- key-range chunks of a layer's candidates -----------------------------------------------
@@ -400,12 +485,12 @@ cudaError_t launch_expand_all(const GenSM* d_gens, int k, const uint64_t* in, un
 
 namespace {
 
-// The passes of one sort.  Input: `in` keys, or the candidates of src (gen).  Pass p writes
-// bufs[(P - 1 - p) & 1], so the last pass writes bufs[0].  The error word and the descriptors
-// are cleared first (one memset); the caller zeroes nothing.
-cudaError_t radix_passes(const uint64_t* in, const ExpandSrc* src, unsigned long long n, int bits,
+// The passes of one sort, over key bits [lo, bits).  Input: `in` keys, or the candidates of src
+// (gen).  Pass p writes bufs[(P - 1 - p) & 1], so the last pass writes bufs[0].  The error word
+// and the descriptors are cleared first (one memset); the caller zeroes nothing.
+cudaError_t radix_passes(const uint64_t* in, const ExpandSrc* src, unsigned long long n, int bits, int lo,
                          uint64_t* const bufs[2], const SortScratch& s, cudaStream_t st) {
-    const int P = passes_of(bits < 1 ? 1 : bits);
+    const int P = passes_of(bits - lo < 1 ? 1 : bits - lo);
     const int nt = tiles_of(n);
     const size_t reset = al(sizeof(unsigned long long) * kSortMaxPasses * kDigits) + 256 + al((size_t)nt * kDigits * 8);
     cudaError_t e = cudaMemsetAsync(s.ghist, 0, reset, st);
@@ -413,17 +498,17 @@ cudaError_t radix_passes(const uint64_t* in, const ExpandSrc* src, unsigned long
     const ExpandSrc none{};
     unsigned long long hb = (n + kBlock - 1) / kBlock;
     if (hb > 152ull * 4) hb = 152ull * 4;
-    if (src) hist_all_kernel<true><<<(unsigned)hb, kBlock, 0, st>>>(nullptr, *src, n, P, s.ghist);
-    else hist_all_kernel<false><<<(unsigned)hb, kBlock, 0, st>>>(in, none, n, P, s.ghist);
+    if (src) hist_all_kernel<true><<<(unsigned)hb, kBlock, 0, st>>>(nullptr, *src, n, P, lo, s.ghist);
+    else hist_all_kernel<false><<<(unsigned)hb, kBlock, 0, st>>>(in, none, n, P, lo, s.ghist);
     const uint64_t* cur = in;
     for (int p = 0; p < P; ++p) {
         uint64_t* dst = bufs[(P - 1 - p) & 1];
         if (p == 0 && src)
-            onesweep_kernel<true><<<nt, kBlock, 0, st>>>(nullptr, *src, dst, n, kRadixBits * p,
+            onesweep_kernel<true><<<nt, kBlock, 0, st>>>(nullptr, *src, dst, n, lo + kRadixBits * p,
                                                          s.ghist + p * kDigits, s.desc, s.ctl + p,
                                                          (unsigned)(p + 1), s.err);
         else
-            onesweep_kernel<false><<<nt, kBlock, 0, st>>>(cur, none, dst, n, kRadixBits * p,
+            onesweep_kernel<false><<<nt, kBlock, 0, st>>>(cur, none, dst, n, lo + kRadixBits * p,
                                                           s.ghist + p * kDigits, s.desc, s.ctl + p,
                                                           (unsigned)(p + 1), s.err);
         cur = dst;
@@ -433,29 +518,29 @@ cudaError_t radix_passes(const uint64_t* in, const ExpandSrc* src, unsigned long
 
 }  // namespace
 
-// Sort keys[0, n) ascending on their low `bits` bits (higher bits must be zero), in place; an
-// odd number of 8-bit passes ends with one copy back.
+// Sort keys[0, n) ascending on their bits [lo, bits) (higher bits must be zero; lower bits
+// decided by the others), in place; an odd number of 8-bit passes ends with one copy back.
 cudaError_t launch_radix_sort(uint64_t* keys, unsigned long long n, int bits, const SortScratch& s,
-                              cudaStream_t st) {
+                              cudaStream_t st, int lo) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     if (n <= 1) return cudaSuccess;
-    const int P = passes_of(bits);
+    const int P = passes_of(bits - lo < 1 ? 1 : bits - lo);
     uint64_t* bufs[2];
     if (P % 2 == 0) { bufs[0] = keys; bufs[1] = s.keys_tmp; }
     else { bufs[0] = s.keys_tmp; bufs[1] = keys; }
-    cudaError_t e = radix_passes(keys, nullptr, n, bits, bufs, s, st);
+    cudaError_t e = radix_passes(keys, nullptr, n, bits, lo, bufs, s, st);
     if (e == cudaSuccess && P % 2 == 1)
         e = cudaMemcpyAsync(keys, s.keys_tmp, n * 8, cudaMemcpyDeviceToDevice, st);
     return e;
 }
 
 cudaError_t launch_expand_sort(const ExpandSrc& src, uint64_t* out, int bits, const SortScratch& s,
-                               cudaStream_t st) {
+                               cudaStream_t st, int lo) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     const unsigned long long n = src.F * (unsigned long long)src.k;
     if (n == 0) return cudaSuccess;
     uint64_t* bufs[2] = {out, s.keys_tmp};
-    return radix_passes(nullptr, &src, n, bits, bufs, s, st);
+    return radix_passes(nullptr, &src, n, bits, lo, bufs, s, st);
 }
 
 // out = keys of sorted a that are first of their run and absent from every sorted b_j,
@@ -477,14 +562,16 @@ cudaError_t launch_unique_difference(const uint64_t* a, unsigned long long na, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_candidate_hist(const ExpandSrc& src, int bits, const SortScratch& s, cudaStream_t st) {
+cudaError_t launch_candidate_hist(const ExpandSrc& src, int bits, const SortScratch& s, cudaStream_t st,
+                                  int lo) {
     (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
     const unsigned long long n = src.F * (unsigned long long)src.k;
     cudaError_t e = cudaMemsetAsync(s.ghist, 0, sizeof(unsigned long long) * kSortMaxPasses * kDigits, st);
     if (e != cudaSuccess || n == 0) return e;
     unsigned long long hb = (n + kBlock - 1) / kBlock;
     if (hb > 152ull * 4) hb = 152ull * 4;
-    hist_all_kernel<true><<<(unsigned)hb, kBlock, 0, st>>>(nullptr, src, n, passes_of(bits), s.ghist);
+    hist_all_kernel<true><<<(unsigned)hb, kBlock, 0, st>>>(nullptr, src, n, passes_of(bits - lo < 1 ? 1 : bits - lo),
+                                                          lo, s.ghist);
     return cudaGetLastError();
 }
 
@@ -507,6 +594,6 @@ cudaError_t launch_mask_keys(uint64_t* keys, unsigned long long n, uint64_t mask
     return cudaGetLastError();
 }
 
-int sort_passes(int bits) { return passes_of(bits < 1 ? 1 : bits); }
+int sort_passes(int bits, int lo) { return passes_of(bits - lo < 1 ? 1 : bits - lo); }
 
 }  // namespace cg
