@@ -410,6 +410,7 @@ struct cg_growth {
     uint64_t cand_cap = 0;
     void* d_sort_scratch = nullptr;
     unsigned long long* d_count = nullptr;
+    cg::SmallSteps* d_small = nullptr;           // state of the one-block small layer steps
     uint64_t* last_layer_ptr = nullptr;   // device pointer of the last reported layer
     uint64_t last_layer_n = 0;
     std::vector<uint64_t> sort_layers;
@@ -469,7 +470,8 @@ struct cg_growth {
         dev_free(d_cand, st);
         dev_free(d_sort_scratch, st);
         dev_free(d_count, st);
-        d_cand = nullptr; d_sort_scratch = nullptr; d_count = nullptr;
+        dev_free(d_small, st);
+        d_cand = nullptr; d_sort_scratch = nullptr; d_count = nullptr; d_small = nullptr;
         L_cap = cand_cap = 0;
     }
 };
@@ -975,6 +977,56 @@ int sort_steps(cg_growth* h, cudaStream_t st, int cur, int prev, uint64_t Fcur, 
     int status = cg::kRunning;
     while (status == cg::kRunning) {
         if (h->max_radius >= 0 && radius >= h->max_radius) { status = cg::kTruncRadius; break; }
+        if ((uint64_t)h->k * Fcur <= (uint64_t)cg::kSmallStep && Fprev <= (uint64_t)cg::kSmallStep) {
+            // small steps, back to back in one block (sort_path.cu): the three layer buffers
+            // hold kSmallStep keys at least
+            rc = ensure_layer(h, cur, cg::kSmallStep, Fcur, st);
+            if (rc == CG_OK) rc = ensure_layer(h, prev, cg::kSmallStep, Fprev, st);
+            if (rc == CG_OK) rc = ensure_layer(h, nxt, cg::kSmallStep, 0, st);
+            if (rc == CG_OK && !h->d_small) {
+                h->d_small = (cg::SmallSteps*)dev_alloc(sizeof(cg::SmallSteps), st);
+                if (!h->d_small) rc = CG_ENOMEM;
+            }
+            if (fail_mem(rc)) { status = cg::kNeedMem; break; }
+            if (rc) return rc;
+            cg::SmallSteps ss{};
+            ss.cur = cur;
+            ss.prev = prev;
+            ss.radius = radius;
+            ss.status = cg::kRunning;
+            ss.Fcur = Fcur;
+            ss.Fprev = Fprev;
+            const size_t head = offsetof(cg::SmallSteps, sizes);
+            if ((e = cudaMemcpyAsync(h->d_small, &ss, head, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_rc(e);
+            if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cg::launch_small_steps(h->d_gens, h->k, h->d_L[0], h->d_L[1], h->d_L[2], h->max_radius,
+                                            h->stop_above, (int)h->sort_layers.size(), h->d_small, st)) !=
+                cudaSuccess)
+                return cuda_rc(e);
+            if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
+            if ((e = cudaMemcpyAsync(&ss, h->d_small, sizeof(ss), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_rc(e);
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_rc(e);
+            h->stats.launches += 1;
+            h->stats.h2d_bytes += head;
+            h->stats.d2h_bytes += sizeof(ss);
+            h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
+            h->stats.rounds += ss.nsteps;
+            if (ss.nsteps < 0 || ss.nsteps > cg::kSmallMaxSteps || ss.cur < 0 || ss.cur > 2 || ss.prev < 0 ||
+                ss.prev > 2 || ss.cur == ss.prev)
+                return CG_EDEVICE;
+            for (int i = 0; i < ss.nsteps; ++i) h->sort_layers.push_back(ss.sizes[i]);
+            cur = ss.cur;
+            prev = ss.prev;
+            nxt = 3 - cur - prev;
+            radius = ss.radius;
+            Fcur = ss.Fcur;
+            Fprev = ss.Fprev;
+            status = ss.status;
+            if (status != cg::kRunning) break;
+            if (ss.nsteps > 0) continue;
+        }
         const uint64_t C = (uint64_t)h->k * Fcur;
         // the next layer's first buffer: the growth ratio of the last step, with a margin
         const double ratio = Fprev > 0 ? (double)Fcur / (double)Fprev : (double)h->k;

@@ -67,4 +67,29 @@ cudaError_t launch_expand_filter(const ExpandSrc& src, int shift, unsigned d0, u
 // keys[i] &= mask, i < n.
 cudaError_t launch_mask_keys(uint64_t* keys, unsigned long long n, uint64_t mask, cudaStream_t st);
 
+// ---- small layer steps in one block ----------------------------------------------------------
+// Layer steps whose k F_r candidates, F_r and F_{r-1} are at most kSmallStep run back to back by
+// one block in shared memory (candidates generated, bitonic-sorted, first of run and absent from
+// L_r and L_{r-1} kept, compacted in order into the third layer buffer), with the stop tests of
+// the host's loop, until a step is too large or the growth stops: one launch and no host round
+// trip for the first and last layers of a growth.
+constexpr int kSmallStep = 4096;
+constexpr int kSmallMaxSteps = 256;
+
+struct SmallSteps {                 // device memory, read and written by the kernel
+    int cur, prev;                  // layer buffers of L_r and L_{r-1} (the third receives L_{r+1})
+    int radius;
+    int status;                     // kRunning: stopped at a step too large for one block
+    unsigned long long Fcur, Fprev;
+    int nsteps;                     // steps run by this launch
+    int pad;
+    unsigned long long sizes[kSmallMaxSteps];   // |L_{r+1}| of each of them
+};
+
+// L[3]: the three layer buffers (each of at least kSmallStep keys); layers_done: layer sizes
+// recorded before this launch (the layer array holds at most kMaxLayers).
+cudaError_t launch_small_steps(const GenSM* d_gens, int k, uint64_t* L0, uint64_t* L1, uint64_t* L2,
+                               int max_radius, unsigned long long stop_above, int layers_done,
+                               SmallSteps* d_state, cudaStream_t st);
+
 }  // namespace cg

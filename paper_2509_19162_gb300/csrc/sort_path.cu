@@ -432,6 +432,144 @@ __global__ void mask_keys_kernel(uint64_t* keys, unsigned long long n, uint64_t 
         keys[i] &= mask;
 }
 
+// ---- small layer steps in one block ----------------------------------------------------------
+constexpr int kSmallBlock = 1024;
+constexpr int kSmallPer = kSmallStep / kSmallBlock;     // candidates per thread
+
+__device__ __forceinline__ unsigned small_lower_bound(const uint64_t* s, unsigned n, uint64_t key) {
+    unsigned lo = 0, hi = n;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (s[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// One block; dynamic shared memory: candidates | L_r | L_{r-1}, kSmallStep keys each.
+__global__ void __launch_bounds__(kSmallBlock)
+small_steps_kernel(const GenSM* __restrict__ gens, int k, uint64_t* L0, uint64_t* L1, uint64_t* L2,
+                   int max_radius, unsigned long long stop_above, int layers_done, SmallSteps* S) {
+    extern __shared__ uint64_t s_small[];
+    uint64_t* A = s_small;
+    uint64_t* Lc = s_small + kSmallStep;
+    uint64_t* Lp = s_small + 2 * kSmallStep;
+    __shared__ unsigned s_w[kSmallBlock / 32];
+    __shared__ int s_stop;
+    uint64_t* L[3] = {L0, L1, L2};
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int cur = S->cur, prev = S->prev, radius = S->radius, nsteps = 0, status = kRunning;
+    unsigned long long Fcur = S->Fcur, Fprev = S->Fprev;
+    for (;;) {
+        // the host loop's tests, in its order
+        if (max_radius >= 0 && radius >= max_radius) { status = kTruncRadius; break; }
+        const unsigned long long C = (unsigned long long)k * Fcur;
+        if (C > (unsigned long long)kSmallStep || Fprev > (unsigned long long)kSmallStep || C == 0 ||
+            nsteps >= kSmallMaxSteps)
+            break;
+        const int nxt = 3 - cur - prev;
+        const unsigned nc = (unsigned)C, fc = (unsigned)Fcur, fp = (unsigned)Fprev;
+        unsigned P = 1;
+        while (P < nc) P <<= 1;
+        for (unsigned i = tid; i < fc; i += kSmallBlock) Lc[i] = L[cur][i];
+        for (unsigned i = tid; i < fp; i += kSmallBlock) Lp[i] = L[prev][i];
+        __syncthreads();
+        // candidate i: generator i / F on state i mod F; padding sorts last
+        for (unsigned i = tid; i < P; i += kSmallBlock) {
+            if (i < nc) {
+                const unsigned g = i / fc;
+                A[i] = apply_gen(gens[g], Lc[i - g * fc]);
+            } else {
+                A[i] = ~0ull;
+            }
+        }
+        __syncthreads();
+        // bitonic sort of A[0, P)
+        for (unsigned kk = 2; kk <= P; kk <<= 1) {
+            for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+                for (unsigned i = tid; i < P; i += kSmallBlock) {
+                    const unsigned p = i ^ j;
+                    if (p > i) {
+                        const uint64_t a = A[i], b = A[p];
+                        if ((a > b) == ((i & kk) == 0)) {
+                            A[i] = b;
+                            A[p] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // thread t: candidates [t kSmallPer, (t + 1) kSmallPer): first of run, not in L_r, L_{r-1}
+        unsigned keep = 0, cnt = 0;
+#pragma unroll
+        for (int q = 0; q < kSmallPer; ++q) {
+            const unsigned i = (unsigned)tid * kSmallPer + q;
+            if (i < nc) {
+                const uint64_t key = A[i];
+                bool kp = i == 0 || A[i - 1] != key;
+                if (kp) {
+                    const unsigned a = small_lower_bound(Lc, fc, key);
+                    if (a < fc && Lc[a] == key) kp = false;
+                }
+                if (kp) {
+                    const unsigned b = small_lower_bound(Lp, fp, key);
+                    if (b < fp && Lp[b] == key) kp = false;
+                }
+                keep |= (unsigned)kp << q;
+                cnt += kp;
+            }
+        }
+        // exclusive scan of the counts over threads (thread order = candidate order)
+        unsigned x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned v = lane < kSmallBlock / 32 ? s_w[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (lane < kSmallBlock / 32) s_w[lane] = v;
+        }
+        __syncthreads();
+        unsigned pos = (wid ? s_w[wid - 1] : 0u) + x - cnt;
+        const unsigned Fn = s_w[kSmallBlock / 32 - 1];
+#pragma unroll
+        for (int q = 0; q < kSmallPer; ++q)
+            if (keep >> q & 1u) L[nxt][pos++] = A[(unsigned)tid * kSmallPer + q];
+        __syncthreads();                        // A, Lc, Lp and s_w are reused by the next step
+        if (Fn == 0) { status = kDone; break; }
+        if (tid == 0) S->sizes[nsteps] = Fn;
+        ++nsteps;
+        ++radius;
+        prev = cur;
+        cur = nxt;
+        Fprev = Fcur;
+        Fcur = Fn;
+        if (stop_above > 0 && Fn > stop_above) { status = kTruncAbove; break; }
+        if (layers_done + nsteps >= kMaxLayers) { status = kTruncRadius; break; }
+        // the new layer is read back by every thread next step: its writes must be visible
+        __threadfence_block();
+        __syncthreads();
+    }
+    (void)s_stop;
+    if (tid == 0) {
+        S->cur = cur;
+        S->prev = prev;
+        S->radius = radius;
+        S->status = status;
+        S->Fcur = Fcur;
+        S->Fprev = Fprev;
+        S->nsteps = nsteps;
+    }
+}
+
 int tiles_of(unsigned long long n) { return (int)((n + kTile - 1) / kTile); }
 
 int passes_of(int bits) { return (bits + kRadixBits - 1) / kRadixBits; }
@@ -595,5 +733,24 @@ cudaError_t launch_mask_keys(uint64_t* keys, unsigned long long n, uint64_t mask
 }
 
 int sort_passes(int bits, int lo) { return passes_of(bits - lo < 1 ? 1 : bits - lo); }
+
+cudaError_t launch_small_steps(const GenSM* d_gens, int k, uint64_t* L0, uint64_t* L1, uint64_t* L2,
+                               int max_radius, unsigned long long stop_above, int layers_done,
+                               SmallSteps* d_state, cudaStream_t st) {
+    (void)cudaGetLastError();   // clear a stale error: the check after the launch is about this one
+    const size_t smem = 3 * (size_t)kSmallStep * sizeof(uint64_t);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(small_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    small_steps_kernel<<<1, kSmallBlock, smem, st>>>(d_gens, k, L0, L1, L2, max_radius, stop_above, layers_done,
+                                                      d_state);
+    return cudaGetLastError();
+}
 
 }  // namespace cg
