@@ -628,9 +628,13 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                 if (d + 1 < total) pending = d + 1;
                 return d;
             };
+            unsigned long long u1 = 0;              // units of slot cur: [u0, u1)
             for (unsigned long long u = next_unit(); u != ~0ull; u = next_unit()) {
-                const int slot = find_job(ubeg, nj, u);
-                if (slot != cur) {
+                // a warp's units mostly stay within one job: search the table only on leaving it
+                if (cur >= 0 && u >= u0 && u < u1) {
+                    // same job as the previous unit
+                } else {
+                    const int slot = find_job(ubeg, nj, u);
                     if (J) stage_flush(buf, cnt, J, c, lane);
                     cur = slot;
                     J = jobs + (act ? __ldcg(act + slot) : slot);
@@ -638,6 +642,7 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     lo = ld_relaxed_ull(&J->lo);
                     hi = ld_relaxed_ull(&J->hi);
                     u0 = ld_relaxed_ull(ubeg + slot);
+                    u1 = ld_relaxed_ull(ubeg + slot + 1);
                 }
                 if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
                 for (int sub = 0; sub < umult; ++sub) {
