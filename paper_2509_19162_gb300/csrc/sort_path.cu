@@ -454,7 +454,6 @@ small_steps_kernel(const GenSM* __restrict__ gens, int k, uint64_t* L0, uint64_t
     uint64_t* Lc = s_small + kSmallStep;
     uint64_t* Lp = s_small + 2 * kSmallStep;
     __shared__ unsigned s_w[kSmallBlock / 32];
-    __shared__ int s_stop;
     uint64_t* L[3] = {L0, L1, L2};
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int cur = S->cur, prev = S->prev, radius = S->radius, nsteps = 0, status = kRunning;
@@ -558,7 +557,6 @@ small_steps_kernel(const GenSM* __restrict__ gens, int k, uint64_t* L0, uint64_t
         __threadfence_block();
         __syncthreads();
     }
-    (void)s_stop;
     if (tid == 0) {
         S->cur = cur;
         S->prev = prev;
