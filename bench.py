@@ -515,15 +515,20 @@ def measure_batch(cg, spec, stream, flush, steps, warmup, autotune=True, tune_ta
             "kernel_ms": kernel_ms, "launches": launches, "variant": variant, "tuned": tuned}
 
 
-def one_at_a_time(cg, jobs, stream, mem_cap=0, strategies=None):
-    """Jobs run one after another through growth() on the same GPU: (layers, seconds)."""
+def one_at_a_time(cg, jobs, stream, mem_cap=0, strategies=None, per_job=None):
+    """Jobs run one after another through growth() on the same GPU: (layers, seconds).  per_job:
+    a list that receives each job's seconds."""
     import torch
     strategies = strategies or ["auto"] * len(jobs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out = [cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=mem_cap, strategy=s,
-                     stream=stream).layers
-           for j, s in zip(jobs, strategies)]
+    out = []
+    for j, s in zip(jobs, strategies):
+        t = time.perf_counter()
+        out.append(cg.growth(j.n, j.gens, j.inverse_closed, j.max_radius, mem_cap=mem_cap, strategy=s,
+                             stream=stream).layers)
+        if per_job is not None:
+            per_job.append(time.perf_counter() - t)
     return out, time.perf_counter() - t0
 
 
@@ -631,8 +636,26 @@ def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=8, job_m
     # the sorted step, which the server does not make either)
     strat = [p["visited"] for p in plans[:lam_sample]]
     one_at_a_time(cg, sample[:10], stream, mem_cap=share, strategies=strat[:10])
-    alone, one_s = one_at_a_time(cg, sample, stream, mem_cap=share, strategies=strat)
+    per_job = []
+    alone, one_s = one_at_a_time(cg, sample, stream, mem_cap=share, strategies=strat, per_job=per_job)
     lam1 = len(sample) / one_s
+    # where one-at-a-time time goes: jobs the server grows alone (each fills the GPU) and the
+    # jobs it batches -- and those batched jobs alone against served together (all queued at once)
+    solo = [p["alone"] for p in plans]
+    small = [j for j, a in zip(jobs, solo) if not a]
+    small_alone_s = []
+    one_at_a_time(cg, small, stream, mem_cap=share,
+                  strategies=[p["visited"] for p, a in zip(plans, solo) if not a], per_job=small_alone_s)
+    with Server(mem_budget=SERVE_BUDGET, max_slots=slots, job_mem_cap=share, rounds_per_step=rounds) as srv:
+        t0 = time.perf_counter()
+        serve_stream(small, [0.0] * len(small), srv, stream, realtime=False)
+        small_served_s = time.perf_counter() - t0
+    split = {"sample_jobs": len(sample),
+             "sample_alone_s_grown_alone_by_server": sum(t for t, a in zip(per_job, solo) if a),
+             "sample_alone_s_batched_by_server": sum(t for t, a in zip(per_job, solo) if not a),
+             "jobs_grown_alone_by_server": sum(solo), "jobs_batched_by_server": len(small),
+             "batched_jobs_one_at_a_time_s": sum(small_alone_s),
+             "batched_jobs_served_together_s": small_served_s}
     out = []
     for mult in rates:
         lam = lam1 * mult
@@ -661,7 +684,8 @@ def measure_serve(cg, jobs, stream, rates=(1.0, 2.0), slots=512, rounds=8, job_m
             "mem_cap_all_predicted_over_share": set(memcap_ended) <= set(over),
             "clocks": clocks})
     return lam1, {"jobs": len(jobs), "job_share_bytes": share, "budget_bytes": SERVE_BUDGET,
-                  "predicted_over_share": len(over), "predicted_over_share_ids": over[:50]}, out
+                  "predicted_over_share": len(over), "predicted_over_share_ids": over[:50],
+                  "time_split": split}, out
 
 
 def run_serve(args):

@@ -291,8 +291,9 @@ int cg_batch_destroy(cg_batch_t b);
  * inverse-closed, k^r otherwise, and never more than the group order), stored with the cheaper
  * visited set (hash table, or the rank bitmap for n <= 14), capped at job_mem_cap bytes per job,
  * the job's share of the budget (a job that needs more stops with CG_TRUNC_MEMCAP; its reported
- * layers are exact).  A job predicted to reach at least 2^24 states fills the GPU by itself: when
- * it reaches the head of the queue, cg_server_step grows it alone with the single-job kernels
+ * layers are exact).  A job predicted to reach at least CG_SERVER_SOLO_STATES states fills the
+ * GPU by itself: when it reaches the head of the queue, cg_server_step grows it alone with the
+ * single-job kernels
  * (same visited set and share, so the same layers) before the batched launch.  Each
  * cg_server_step admits what fits, then runs up to rounds_per_step layer steps of
  * every admitted job in one persistent launch on the caller's stream (jobs' states stay on the
@@ -317,6 +318,7 @@ int cg_batch_destroy(cg_batch_t b);
  *                      (CG_STRATEGY_HASH or CG_STRATEGY_BITMAP).  Any output may be NULL.
  *                      Errors: CG_EINVAL, CG_ENOTCLOSED.
  */
+#define CG_SERVER_SOLO_STATES (1u << 24)
 typedef struct cg_server* cg_server_t;
 int cg_server_create(uint64_t mem_budget, int max_slots, uint64_t job_mem_cap, int rounds_per_step,
                      cg_server_t* out);

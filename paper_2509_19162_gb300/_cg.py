@@ -43,6 +43,7 @@ CG_OPT_ILP = 5
 CG_OPT_SWEEP_ORDER = 9
 CG_NOALLOC_MAX_STATES = 1 << 20
 CG_NOALLOC_MAX_GENS = 256
+CG_SERVER_SOLO_STATES = 1 << 24
 
 # Every symbol include/cg_growth.h declares: name -> (restype, argtypes)
 _u8p = ctypes.POINTER(ctypes.c_uint8)

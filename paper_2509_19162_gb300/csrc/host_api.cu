@@ -2280,7 +2280,7 @@ constexpr int kSrvMaxGens = 128;     // generators per job
 // A job predicted to reach at least this many states fills the GPU by itself: it is grown
 // alone by the single-job kernels (the fastest for it) when it reaches the head of the queue,
 // and the smaller jobs around it are batched.
-constexpr uint64_t kSrvSoloStates = 1ull << 24;
+constexpr uint64_t kSrvSoloStates = CG_SERVER_SOLO_STATES;
 constexpr int kSrvLayers = 4096;     // layer sizes kept per job (more: CG_TRUNC_RADIUS)
 
 // Upper bound on the states a job visits up to its radius cap: sphere r of a graph of

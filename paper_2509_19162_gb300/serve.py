@@ -45,7 +45,9 @@ class Server:
                 max_radius: int = -1, job_mem_cap: int = 160 << 24) -> Dict[str, int]:
         """Admission plan of a job under the per-job share job_mem_cap (bytes; the server's default
         share is its budget / 64): predicted states up to the radius cap, states granted, the
-        device bytes it is admitted with, and its visited set ("hash" or "bitmap").  Host only."""
+        device bytes it is admitted with, its visited set ("hash" or "bitmap"), and whether the
+        server grows it alone (predicted to fill the GPU: CG_SERVER_SOLO_STATES states or more).
+        Host only."""
         g = _gens_bytes(n, gens)
         if inverse_closed is None:
             inverse_closed = _is_inverse_closed(gens)
@@ -56,7 +58,8 @@ class Server:
                                         ctypes.byref(st), ctypes.byref(gr), ctypes.byref(by), ctypes.byref(vis)),
                   "cg_server_predict")
         return {"states": int(st.value), "granted": int(gr.value), "bytes": int(by.value),
-                "visited": "bitmap" if vis.value == _cg.CG_STRATEGY_BITMAP else "hash"}
+                "visited": "bitmap" if vis.value == _cg.CG_STRATEGY_BITMAP else "hash",
+                "alone": int(st.value) >= _cg.CG_SERVER_SOLO_STATES}
 
     def step(self, stream=None):
         a = ctypes.c_int(0)
