@@ -262,6 +262,27 @@ __device__ __forceinline__ uint64_t perm_rank(uint64_t key, int n) {
     return (uint64_t)top * 479001600ull + low;
 }
 
+// The rank with n known at run time but the same for a whole warp (one job): the loop compiled
+// for that n, through a switch.
+__device__ __forceinline__ uint64_t perm_rank_uniform(uint64_t key, int n) {
+    switch (n) {
+        case 2: return perm_rank_n<2>(key);
+        case 3: return perm_rank_n<3>(key);
+        case 4: return perm_rank_n<4>(key);
+        case 5: return perm_rank_n<5>(key);
+        case 6: return perm_rank_n<6>(key);
+        case 7: return perm_rank_n<7>(key);
+        case 8: return perm_rank_n<8>(key);
+        case 9: return perm_rank_n<9>(key);
+        case 10: return perm_rank_n<10>(key);
+        case 11: return perm_rank_n<11>(key);
+        case 12: return perm_rank_n<12>(key);
+        case 13: return perm_rank_n<13>(key);
+        case 14: return perm_rank_n<14>(key);
+        default: return perm_rank(key, n);
+    }
+}
+
 // Visited test-and-set of G keys in a rank-indexed bitmap (one bit per element of S_n): one
 // atomicOr per key, whose returned word says whether the bit was already set (a single L2
 // round trip whether the key is new or not).  res[i] = 1 if this call set the bit, 0 if it
@@ -275,7 +296,7 @@ __device__ __forceinline__ void bitmap_insert_multi(unsigned* bm, uint64_t words
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         res[i] = 0;
-        const uint64_t r = N > 0 ? perm_rank_n<(N > 0 ? N : 1)>(key[i]) : perm_rank(key[i], n);
+        const uint64_t r = N > 0 ? perm_rank_n<(N > 0 ? N : 1)>(key[i]) : perm_rank_uniform(key[i], n);
         w[i] = r >> 5;
         bit[i] = 1u << (unsigned)(r & 31u);
         if ((vmask >> i & 1u) && w[i] >= words) res[i] = -1;

@@ -541,6 +541,9 @@ constexpr unsigned long long kSoloUnits = kGrowBlock / 32;
 
 // Generators of a single job kept in shared memory when there are at most this many.
 constexpr int kSmemGens = 32;
+// Several jobs: each warp keeps the generators of its current job in shared memory when the job
+// has at most this many.
+constexpr int kWarpGens = 10;
 
 // kMulti = false: the launch has exactly one job (the single-job path only is compiled, which
 // keeps registers low), whose static fields are `jc`; true: any number of jobs (`jc` unused).
@@ -551,6 +554,8 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
     __shared__ uint64_t s_stage[kGrowBlock / 32][kStage];
     __shared__ GenSM s_gens[kSmemGens];
     __shared__ unsigned long long s_unit;
+    __shared__ JobConst s_jc[kMulti ? kGrowBlock / 32 : 1];
+    __shared__ GenSM s_wgens[kMulti ? kGrowBlock / 32 : 1][kMulti ? kWarpGens : 1];
     const GenSM* single_gens = jobs[0].gens;
     if (!kMulti && jobs[0].k <= kSmemGens) {
         for (int j = threadIdx.x; j < jobs[0].k; j += blockDim.x) s_gens[j] = jobs[0].gens[j];
@@ -602,7 +607,11 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
         } else {
             int cur = -1;
             JobDev* J = nullptr;
-            JobConst c = {};
+            // the current job's static fields, one copy per warp in shared memory (read where
+            // used, which keeps them out of the registers)
+            JobConst& c = s_jc[threadIdx.x >> 5];
+            const GenSM* jg = nullptr;              // the current job's generators
+            int ovf = 0;                            // the current job's overflow flag, read a unit ago
             unsigned long long lo = 0, hi = 0, u0 = 0;
             const unsigned long long ue = stat * (blockIdx.x + 1) / gridDim.x;
             unsigned long long pending = ~0ull;
@@ -638,23 +647,45 @@ hash_grow_kernel(JobDev* jobs, int njobs, unsigned long long* ubeg, Ctl* ctl, in
                     if (J) stage_flush(buf, cnt, J, c, lane);
                     cur = slot;
                     J = jobs + (act ? __ldcg(act + slot) : slot);
-                    c = job_const(J);
+                    if (lane == 0) c = job_const(J);
+                    __syncwarp();
+                    ovf = 0;
+                    jg = J->gens;
+                    if (kMulti && c.k <= kWarpGens) {
+                        // copy them into this warp's shared slots, word by word across the lanes
+                        GenSM* dst = s_wgens[threadIdx.x >> 5];
+                        const unsigned words = (unsigned)c.k * (unsigned)(sizeof(GenSM) / 4);
+                        const unsigned* from = reinterpret_cast<const unsigned*>(jg);
+                        unsigned* to = reinterpret_cast<unsigned*>(dst);
+                        for (unsigned i = lane; i < words; i += 32) to[i] = from[i];
+                        __syncwarp();
+                        jg = dst;
+                    }
                     lo = ld_relaxed_ull(&J->lo);
                     hi = ld_relaxed_ull(&J->hi);
                     u0 = ld_relaxed_ull(ubeg + slot);
                     u1 = ld_relaxed_ull(ubeg + slot + 1);
                 }
-                if (__any_sync(0xffffffffu, ld_relaxed_int(&J->overflow))) continue;
-                for (int sub = 0; sub < umult; ++sub) {
-                    const unsigned long long first = lo + (((u - u0) * (unsigned long long)umult + sub) << 5);
-                    if (first >= hi) break;
+                // A job whose buffers ran full stops expanding (the host grows them or reports
+                // the exact layers so far): its flag, read while the previous unit of the same
+                // job ran, skips the rest of its units.
+                if (__any_sync(0xffffffffu, ovf)) continue;
+                ovf = ld_relaxed_int(&J->overflow);
+                // the unit's unit_mult groups of 32 states, the next group's keys loaded while one
+                // is expanded
+                unsigned long long first = lo + (((u - u0) * (unsigned long long)umult) << 5);
+                uint64_t s_nx = first + lane < hi ? __ldcg(c.keys + first + lane) : 0;
+                for (int sub = 0; sub < umult && first < hi; ++sub) {
                     const unsigned long long idx = first + lane;
-                    const uint64_t s0 = idx < hi ? __ldcg(J->keys + idx) : 0;
+                    const uint64_t s0 = s_nx;
+                    const unsigned long long nf = first + 32;
+                    s_nx = (sub + 1 < umult && nf + lane < hi) ? __ldcg(c.keys + nf + lane) : 0;
                     // In the rank-bitmap variant a launch may mix jobs of both visited-set kinds.
                     if (kMode == kVisitBitmap && c.mode != kVisitBitmap)
-                        do_unit<kProbeILP, kVisitHash>(J, c, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                        do_unit<kProbeILP, kVisitHash>(J, c, jg, idx, hi, buf, cnt, lane, overflow_seen, s0);
                     else
-                        do_unit<kProbeILP, kMode>(J, c, J->gens, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                        do_unit<kProbeILP, kMode>(J, c, jg, idx, hi, buf, cnt, lane, overflow_seen, s0);
+                    first = nf;
                 }
             }
             if (J) stage_flush(buf, cnt, J, c, lane);
