@@ -127,7 +127,8 @@ struct alignas(128) JobDev {
     uint64_t bitmap_words;     // bitmap mode: 32-bit words in `table` (ceil(n!/32))
     uint64_t start_key;        // packed start vector when use_start
     int tagged;                // 1: keys leave bits 60-63 free for the parent-edge tag
-    int pad1;
+    int closed;                // 1: every generator's inverse is in the set (every state but
+                               //    the start carries a parent-edge tag)
     // dynamic, updated between rounds by block 0
     alignas(128) unsigned long long lo;     // frontier = keys[lo, hi)
     unsigned long long hi;

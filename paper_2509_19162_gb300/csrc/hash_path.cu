@@ -359,6 +359,7 @@ struct JobConst {
     int n;
     int tagged;
     int mode;
+    int closed;
 };
 
 __device__ __forceinline__ JobConst job_const(const JobDev* J) {
@@ -372,6 +373,7 @@ __device__ __forceinline__ JobConst job_const(const JobDev* J) {
     c.n = J->n;
     c.tagged = J->tagged;
     c.mode = J->mode;
+    c.closed = J->closed;
     return c;
 }
 
@@ -494,6 +496,40 @@ __device__ __forceinline__ void do_unit(JobDev* J, const JobConst& c, const GenS
     }
 }
 
+// The same work with a lane per (state, generator) pair instead of per state, for rounds in which
+// every warp has at most one unit: a unit is sp = 32 / (k - 1) states, lane l takes state l / (k - 1)
+// and its non-parent generator number l mod (k - 1) (lslot), so that the k - 1 probes of a state
+// are in flight together rather than one after the other.  Every state must carry its parent-edge
+// tag (the set is closed under inverses and the frontier is not the start).
+template <int kMode, int kN = 0>
+__device__ __forceinline__ void do_unit_split(JobDev* J, const JobConst& c, const GenSM* gens, bool active,
+                                              uint64_t s, int lslot, uint64_t* buf, int& cnt, int lane,
+                                              bool& overflow_seen) {
+    const unsigned tag = (unsigned)(s >> 60);   // 1 + generator that leads back to the parent
+    s &= kKeyBits60;
+    // generators 0..tag-2 keep their number, the rest move up by one (idle lanes: lslot itself)
+    const int gi = (active && lslot >= (int)tag - 1) ? lslot + 1 : lslot;
+    uint64_t t[1];
+    int res[1];
+    t[0] = apply_gen<kMode != kVisitBitmap>(gens[gi], s);
+    const unsigned vmask = active ? 1u : 0u;
+    if (kMode == kVisitBitmap)
+        bitmap_insert_multi<1, kN>(reinterpret_cast<unsigned*>(c.table), c.bitmap_words, c.n, t, res, vmask);
+    else if (kMode == 1)
+        table_insert_multi_sector<1>(c.table, c.table_mask, t, res, vmask, kMaxProbe);
+    else
+        table_insert_multi_slot<1>(c.table, c.table_mask, t, res, vmask, kMaxProbe);
+    if (__any_sync(0xffffffffu, res[0] < 0)) {
+        overflow_seen = true;
+        if (lane == 0) atomicExch(&J->overflow, 1);
+    }
+    const unsigned fresh = __ballot_sync(0xffffffffu, res[0] == 1);
+    if (res[0] == 1) buf[cnt + __popc(fresh & lanemask_lt())] = t[0] | (uint64_t)gens[gi].inv_tag << 60;
+    cnt += __popc(fresh);
+    __syncwarp();
+    if (cnt > kStage - 32) stage_flush(buf, cnt, J, c, lane);
+}
+
 // Next work unit of the block for the calling warp (one shared-memory atomic per warp).
 __device__ __forceinline__ unsigned long long draw_unit(unsigned long long& counter, int lane) {
     unsigned long long u = 0;
@@ -515,6 +551,22 @@ __device__ __forceinline__ void phase_single(JobDev* J, const JobConst& c, const
     int cnt = 0;
     bool overflow_seen = false;
     const unsigned long long total = (hi - lo + 31) >> 5;
+    const int m = c.k - 1;                      // generators a tagged state expands
+    if (total <= W && c.tagged && c.closed && lo > 0 && m >= 1 && m <= 32) {
+        // a small round (at most one unit a warp): a lane per (state, generator) pair
+        const int sp = 32 / m;
+        const int lstate = lane / m, lslot = lane - lstate * m;
+        const unsigned long long ts = (hi - lo + (unsigned long long)sp - 1) / (unsigned long long)sp;
+        for (unsigned long long u = w0; u < ts; u += W) {
+            const unsigned long long idx = lo + u * (unsigned long long)sp + (unsigned long long)lstate;
+            const bool active = lstate < sp && idx < hi;
+            const uint64_t s = active ? __ldcg(c.keys + idx) : 0;
+            do_unit_split<kMode, kN>(J, c, gens, active, s, lslot, buf, cnt, lane, overflow_seen);
+            if (overflow_seen) break;
+        }
+        stage_flush_block(buf, cnt, J, c, lane);
+        return;
+    }
     unsigned long long u = w0;
     uint64_t s_next = (u < total && lo + (u << 5) + lane < hi) ? __ldcg(c.keys + lo + (u << 5) + lane) : 0;
     int ov = 0;
@@ -954,6 +1006,7 @@ cudaError_t launch_hash_grow(JobDev* d_jobs, int njobs, unsigned long long* d_ub
         jc.n = host_job->n;
         jc.tagged = host_job->tagged;
         jc.mode = host_job->mode;
+        jc.closed = host_job->closed;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

@@ -546,6 +546,8 @@ void fill_static(cg_growth* h, JobDev& J) {
     J.use_start = h->use_start ? 1 : 0;
     J.start_key = h->start_key;
     J.tagged = h->n * h->width <= 60 ? 1 : 0;
+    J.closed = 1;
+    for (const GenSM& g : h->gsm) J.closed &= g.inv_tag != 0 ? 1 : 0;
 }
 
 int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
