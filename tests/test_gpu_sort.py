@@ -137,6 +137,24 @@ def test_sort_strategy_limits_and_last_layer(cg):
     assert r.status == 2 and r.layers == want[:len(r.layers)]
 
 
+def test_sort_small_steps_stop_inside_one_block(cg):
+    # Steps of at most 4096 candidates run back to back in one block on the device, with the host
+    # loop's stop tests: a radius cap and a layer-size stop that fire inside them, and a growth all
+    # of whose steps are small, whose last layer comes out of those steps.
+    want = oracle.growth(8, w.coxeter(8))[0]
+    r = cg.growth(8, w.coxeter(8), strategy="sort", max_radius=3)
+    assert r.status == 1 and r.layers == want[:4]
+    r = cg.growth(8, w.coxeter(8), strategy="sort", stop_above=100)
+    first = next(i for i, x in enumerate(want) if x > 100)
+    assert r.status == 3 and r.layers == want[:first + 1]
+    g = cg.Growth(6, w.lrx(6), strategy="sort", keep_last=True)
+    r = g.run()
+    assert r.status == 0 and r.layers == oracle.growth(6, w.lrx(6))[0]
+    last = np.sort(np.asarray(g.last_layer(), dtype=np.uint64))
+    g.close()
+    assert np.array_equal(last, oracle.layer_keys(6, w.lrx(6), len(r.layers) - 1))
+
+
 def test_sort_strategy_key_range_chunks(cg):
     # 200 MB holds the three largest layers of S_11 LRX but not their 9.15M candidates at once:
     # the large steps run in key-range chunks (top-digit histogram, then one sort per range)
