@@ -32,6 +32,9 @@ constexpr uint64_t kDefaultMemCap = 160ull << 30;
 constexpr uint64_t kTimeoutNs = 30ull * 1000 * 1000 * 1000;  // per barrier wait
 // A sweep round of all of S_14 can take seconds; a block with no work waits that long.
 constexpr uint64_t kSweepTimeoutNs = 120ull * 1000 * 1000 * 1000;
+// A growth whose rank bitmap exceeds L2 orders frontiers of at least this many states by rank
+// before expanding them (run_hash); smaller ones cost more to order than the L2 hits buy.
+constexpr uint64_t kOrderMinStates = 1ull << 20;
 constexpr double kMaxLoad = 0.5;                                // visited-table load limit
 constexpr uint64_t kExactAllocLimit = 24ull << 30;  // allocate |<S>| states up front below this
 
@@ -607,10 +610,45 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return cuda_rc(e);
         if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return cuda_rc(e);
     }
+    // A rank bitmap larger than L2 takes its random atomics from DRAM.  Keys in ascending order are
+    // in Lehmer-rank order (the value at position n - 1 is the top rank digit, and so on down), and
+    // a generator that moves only positions below j sends a state within j! ranks of it: a frontier
+    // grouped by its top four elements keeps the visited words of most images inside the group's
+    // stretch of the bitmap, which L2 holds while the grid works through it.  Such a growth runs
+    // one round per launch, and a frontier of at least kOrderMinStates states is first put in order
+    // of key bits [4n - 16, 4n) (two stable 8-bit passes; the parent-edge tags ride along), when
+    // the sort's scratch fits beside the job's buffers within mem_cap.
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        l2 = 0;
+    }
+    const bool order_frontier = bitmap && h->start_is_perm && h->width == 4 && h->n >= 8 && l2 > 0 &&
+                                bm_bytes > (uint64_t)l2;
     for (;;) {
         if ((e = cudaEventRecord(h->ev0, st)) != cudaSuccess) return cuda_rc(e);
-        if ((e = cg::launch_hash_grow(h->d_job, 1, h->d_ubeg, h->d_ctl, grid, cg::kMaxLayers + 1,
-                                      kTimeoutNs, ilp, st, h->n, nullptr, &J)) != cudaSuccess)
+        int sort_err = 0;
+        if (order_frontier) {
+            const uint64_t F = J.hi > J.lo ? J.hi - J.lo : 0;
+            const uint64_t need = cg::sort_scratch_bytes(F);
+            if (F >= kOrderMinStates && h->keys_cap * 8 + bm_bytes + need <= mem) {
+                void* scr = dev_alloc(need, st);
+                if (scr) {
+                    const cg::SortScratch sc = cg::carve_sort_scratch(scr, F);
+                    e = cudaMemsetAsync(sc.err, 0, 4, st);
+                    if (e == cudaSuccess)
+                        e = cg::launch_radix_sort(h->d_keys + J.lo, F, 4 * h->n, sc, st, 4 * h->n - 16);
+                    if (e == cudaSuccess) e = cudaMemcpyAsync(&sort_err, sc.err, 4, cudaMemcpyDeviceToHost, st);
+                    dev_free(scr, st);
+                    if (e != cudaSuccess) return cuda_rc(e);
+                    h->stats.launches += 1 + cg::sort_passes(4 * h->n, 4 * h->n - 16);
+                    h->stats.d2h_bytes += 4;
+                }
+            }
+        }
+        if ((e = cg::launch_hash_grow(h->d_job, 1, h->d_ubeg, h->d_ctl, grid,
+                                      order_frontier ? 1 : cg::kMaxLayers + 1, kTimeoutNs, ilp, st, h->n,
+                                      nullptr, &J)) != cudaSuccess)
             return cuda_rc(e);
         if ((e = cudaEventRecord(h->ev1, st)) != cudaSuccess) return cuda_rc(e);
         h->stats.launches += 1;
@@ -624,6 +662,14 @@ int run_hash(cg_growth* h, cudaStream_t st, int* final_status) {
         h->stats.kernel_ms += elapsed_ms(h->ev0, h->ev1);
         h->stats.rounds += ctl.rounds;
         if (ctl.err) return ctl.err;
+        if (sort_err) return sort_err;
+        if (order_frontier && J.status == cg::kRunning) {
+            // the next round, in its own launch
+            if ((e = cg::launch_resume_units(h->d_job, 1, h->d_ubeg, h->d_ctl, st)) != cudaSuccess)
+                return cuda_rc(e);
+            h->stats.launches += 1;
+            continue;
+        }
         if (J.status != cg::kNeedMem) break;
         if (h->keys_cap >= max_cap) break;  // cannot grow: truncated by mem_cap
         // Grow: keep layers 0..radius (keys[0, hi)), rebuild the visited table from them.
